@@ -1,0 +1,191 @@
+"""CPU oracle for the (r,s) nucleus decomposition -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` use
+this package. The CUDA library never imports, links or calls it, and the two share no code:
+the only common module is the seeded input generator package ``graphgen``.
+
+The arithmetic lives in ``nucleus_oracle.c`` (plain sequential C, exact integers); this
+module only compiles it (gcc, no -march flags, so it builds on x86_64 and aarch64 alike)
+and marshals numpy arrays through ctypes.
+
+Functions (each follows the passage named in its docstring):
+
+* ``list_cliques(g, c)``        all c-cliques, lexicographic order of ascending tuples
+* ``count(g, r, s)``            s-clique count of every r-clique (Algorithm 2, Count-Func)
+* ``decompose(g, r, s)``        Algorithm 2's peeling loop with Update/Update-Func, 1/a exact
+* ``decompose_fixpoint(g, r, s)`` the definition of Section 2 written out as nested fixpoints
+* ``local_counts(g, r, s, tuples)`` per-r-clique s-clique counts one by one (sampled checks)
+* ``certify(...)``              validity + elimination-order certificate of a claimed result
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "nucleus_oracle.c")
+_LIB = os.path.join(_HERE, "_liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+LOOKUP_FN = ctypes.CFUNCTYPE(ctypes.c_int64, ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p)
+
+
+def build_lib(force: bool = False) -> str:
+    """Compile the oracle with plain gcc -O2 into ``_liboracle.so``."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _L():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build_lib()
+            lib = ctypes.CDLL(_LIB)
+            i64p = ctypes.POINTER(ctypes.c_int64)
+            i32p = ctypes.POINTER(ctypes.c_int32)
+            g3 = [ctypes.c_int32, i64p, i32p]
+            lib.orc_list_cliques.argtypes = g3 + [ctypes.c_int, i32p, ctypes.c_int64]
+            lib.orc_list_cliques.restype = ctypes.c_int64
+            lib.orc_count.argtypes = g3 + [ctypes.c_int, ctypes.c_int, i64p, i64p, i64p]
+            lib.orc_count.restype = ctypes.c_int
+            lib.orc_decompose.argtypes = g3 + [ctypes.c_int, ctypes.c_int, i32p, i32p, i64p, i64p, i64p,
+                                               ctypes.c_int64, i64p, i64p]
+            lib.orc_decompose.restype = ctypes.c_int
+            lib.orc_decompose_fixpoint.argtypes = g3 + [ctypes.c_int, ctypes.c_int, i32p]
+            lib.orc_decompose_fixpoint.restype = ctypes.c_int
+            lib.orc_certify.argtypes = g3 + [ctypes.c_int, ctypes.c_int, i32p, i32p, i64p, i32p, ctypes.c_int64,
+                                             LOOKUP_FN, ctypes.c_void_p, i64p, i64p]
+            lib.orc_certify.restype = ctypes.c_int
+            lib.orc_local_counts.argtypes = g3 + [ctypes.c_int, ctypes.c_int, i32p, ctypes.c_int64, i64p]
+            lib.orc_local_counts.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _p(a, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def _g(g):
+    rp = np.ascontiguousarray(g.rowptr, dtype=np.int64)
+    col = np.ascontiguousarray(g.col, dtype=np.int32)
+    if col.size == 0:
+        col = np.zeros(1, np.int32)
+    return rp, col, [ctypes.c_int32(g.n), _p(rp, ctypes.c_int64), _p(col, ctypes.c_int32)]
+
+
+def _check(rc: int, what: str):
+    if rc == -1:
+        raise ValueError(f"{what}: unsupported (r, s); the oracle takes 1 <= r < s <= 7")
+    if rc == -2:
+        raise MemoryError(f"{what}: out of memory")
+    if rc != 0:
+        raise RuntimeError(f"{what}: internal inconsistency (rc={rc})")
+
+
+def list_cliques(g, c: int) -> np.ndarray:
+    """All c-cliques as ascending tuples, lexicographic order; shape (n_c, c). Algorithm 1."""
+    rp, col, a = _g(g)
+    n_c = _L().orc_list_cliques(*a, int(c), None, 0)
+    if n_c < 0:
+        raise ValueError("bad clique size")
+    out = np.zeros((max(int(n_c), 1), c), np.int32)
+    _L().orc_list_cliques(*a, int(c), _p(out, ctypes.c_int32), int(n_c))
+    return out[: int(n_c)]
+
+
+def count(g, r: int, s: int):
+    """(counts int64[n_r], n_s): Algorithm 2, Count-Func applied to every s-clique."""
+    rp, col, a = _g(g)
+    n_r = ctypes.c_int64()
+    n_s = ctypes.c_int64()
+    _check(_L().orc_count(*a, r, s, None, ctypes.byref(n_r), ctypes.byref(n_s)), "count")
+    counts = np.zeros(max(n_r.value, 1), np.int64)
+    _check(_L().orc_count(*a, r, s, _p(counts, ctypes.c_int64), ctypes.byref(n_r), ctypes.byref(n_s)), "count")
+    return counts[: n_r.value], int(n_s.value)
+
+
+@dataclass
+class Decomposition:
+    core: np.ndarray  # int32[n_r], canonical order
+    round: np.ndarray  # int32[n_r], round in which each r-clique is peeled
+    rho: int  # number of rounds
+    sizes: np.ndarray  # |A| per round
+    levels: np.ndarray  # k per round
+    n_s: int
+    listed: int  # s-cliques re-listed by Update over the whole run
+    extra: dict = field(default_factory=dict)
+
+
+def decompose(g, r: int, s: int) -> Decomposition:
+    """Algorithm 2 (arb-nucleus-decomp) with Update / Update-Func; exact 1/a."""
+    rp, col, a = _g(g)
+    n_r = ctypes.c_int64()
+    _check(_L().orc_count(*a, r, s, None, ctypes.byref(n_r), None), "decompose")
+    nr = n_r.value
+    core = np.zeros(max(nr, 1), np.int32)
+    rnd = np.zeros(max(nr, 1), np.int32)
+    cap = max(nr, 1)
+    sizes = np.zeros(cap, np.int64)
+    levels = np.zeros(cap, np.int64)
+    rho = ctypes.c_int64()
+    n_s = ctypes.c_int64()
+    listed = ctypes.c_int64()
+    _check(_L().orc_decompose(*a, r, s, _p(core, ctypes.c_int32), _p(rnd, ctypes.c_int32), ctypes.byref(rho),
+                              _p(sizes, ctypes.c_int64), _p(levels, ctypes.c_int64), cap, ctypes.byref(n_s),
+                              ctypes.byref(listed)), "decompose")
+    t = rho.value
+    return Decomposition(core[:nr], rnd[:nr], t, sizes[:t].copy(), levels[:t].copy(), int(n_s.value),
+                         int(listed.value))
+
+
+def decompose_fixpoint(g, r: int, s: int) -> np.ndarray:
+    """Core numbers straight from the definition (Section 2): nested greatest fixpoints."""
+    rp, col, a = _g(g)
+    n_r = ctypes.c_int64()
+    _check(_L().orc_count(*a, r, s, None, ctypes.byref(n_r), None), "fixpoint")
+    core = np.zeros(max(n_r.value, 1), np.int32)
+    _check(_L().orc_decompose_fixpoint(*a, r, s, _p(core, ctypes.c_int32)), "fixpoint")
+    return core[: n_r.value]
+
+
+def local_counts(g, r: int, s: int, tuples: np.ndarray) -> np.ndarray:
+    """s-clique count of each given r-clique (ascending tuples), one by one."""
+    rp, col, a = _g(g)
+    t = np.ascontiguousarray(tuples, dtype=np.int32).reshape(-1, r)
+    out = np.zeros(max(t.shape[0], 1), np.int64)
+    _check(_L().orc_local_counts(*a, r, s, _p(t, ctypes.c_int32), t.shape[0], _p(out, ctypes.c_int64)),
+           "local_counts")
+    return out[: t.shape[0]]
+
+
+def certify(g, r: int, s: int, core: np.ndarray, rnd: np.ndarray, ids: np.ndarray, tuples: np.ndarray, lookup):
+    """Validity / elimination-order supports of the r-cliques ``ids`` (ascending ``tuples``)
+    under a claimed (core, round). ``lookup(tuple) -> canonical id``. Returns two int64 arrays."""
+    rp, col, a = _g(g)
+    core = np.ascontiguousarray(core, dtype=np.int32)
+    rnd = np.ascontiguousarray(rnd, dtype=np.int32)
+    ids = np.ascontiguousarray(ids, dtype=np.int64)
+    t = np.ascontiguousarray(tuples, dtype=np.int32).reshape(-1, r)
+    k = ids.size
+    sv = np.zeros(max(k, 1), np.int64)
+    so = np.zeros(max(k, 1), np.int64)
+
+    def _cb(ptr, user):
+        return int(lookup(tuple(ptr[i] for i in range(r))))
+
+    cb = LOOKUP_FN(_cb)
+    _check(_L().orc_certify(*a, r, s, _p(core, ctypes.c_int32), _p(rnd, ctypes.c_int32), _p(ids, ctypes.c_int64),
+                            _p(t, ctypes.c_int32), k, cb, None, _p(sv, ctypes.c_int64), _p(so, ctypes.c_int64)),
+           "certify")
+    return sv[:k], so[:k]
