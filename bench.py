@@ -1,0 +1,425 @@
+#!/usr/bin/env python
+"""Benchmark of the (r,s) nucleus decomposition hot path on GB300.
+
+One step = the whole hot path for every (r,s) of the workload on a graph already resident in
+HBM: orientation and the edge index, the triangle index (r = 3), s-clique counting and the
+device-resident peeling loop, results left in device memory. Default workload: seeded R-MAT
+scale 20 (2^20 vertices, 16 * 2^20 edge samples, a=0.57 b=0.19 c=0.19), (2,3) then (3,4).
+
+Prints ONE JSON line (rank 0). ``value`` is s-cliques processed per second, counting each
+s-clique once for the count phase and once per member r-clique re-listed by Update:
+(1 + C(s,r)) * n_s per (r,s), summed over the workload's (r,s) and over ranks.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl ours|reference] [--workload NAME]
+
+--impl reference times the CPU oracle (test infrastructure, single-threaded C) on a bounded
+sample of the same workload (a smaller R-MAT with the same parameters), on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import graphgen as gg  # noqa: E402
+
+L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+
+WORKLOADS = {
+    "rmat20": dict(
+        desc="R-MAT scale 20, edge factor 16, a=0.57 b=0.19 c=0.19, symmetrised+deduplicated; (2,3) and (3,4)",
+        gen=lambda: gg.rmat_scale20(seed=2),
+        rs=[(2, 3), (3, 4)],
+        sample=lambda scale: gg.rmat(scale, 16, 0.57, 0.19, 0.19, seed=2),
+        sample_desc="R-MAT scale {scale} (same edge factor, a, b, c and seed), (2,3) and (3,4)",
+    ),
+    "cl2k": dict(
+        desc="Chung-Lu n=2000, avg degree 20, exponent 2.1, max expected degree 200; (2,3)",
+        gen=lambda: gg.chung_lu_2k(seed=1),
+        rs=[(2, 3)],
+        sample=lambda scale: gg.chung_lu_2k(seed=1),
+        sample_desc="the whole workload",
+    ),
+    "cl4m": dict(
+        desc="Chung-Lu n=4,194,304, avg degree 30, exponent 2.3, w_max=sqrt(sum w), + 2000 planted communities "
+             "(20-60 vertices, density 0.7); (3,4) and (2,4), int64 tallies",
+        gen=lambda: gg.chung_lu_4m_planted(seed=3),
+        rs=[(3, 4), (2, 4)],
+        width=8,
+        sample=lambda scale: gg.with_planted(gg.chung_lu(1 << scale, 30.0, 2.3, seed=3, exact=False), 20, 20, 60,
+                                             0.7, 3 + 7919),
+        sample_desc="Chung-Lu n=2^{scale} with the same parameters plus 20 planted communities, (3,4) and (2,4)",
+    ),
+}
+
+
+def units_of(r: int, s: int, n_s: int) -> int:
+    """s-cliques of Algorithm 2: each counted once, then re-listed once per member r-clique."""
+    return (1 + math.comb(s, r)) * n_s
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rmat20")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------------------
+# distributed plumbing (replicas: every rank runs the whole workload; no data-path collective)
+
+def dist_setup(want_nccl: bool):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl" if want_nccl else "gloo")
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg, device=None):
+    if pg is None:
+        return
+    if device is not None:
+        pg.barrier(device_ids=[device])
+    else:
+        pg.barrier()
+
+
+def max_over_ranks(pg, x: float, device=None) -> float:
+    if pg is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=f"cuda:{device}" if device is not None else "cpu")
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------------------------------
+# clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="nd_clocks_", suffix=".csv")
+        os.close(fd)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def gpu_uuid(device: int) -> str | None:
+    try:
+        import torch
+
+        u = str(torch.cuda.get_device_properties(device).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle timing (the baseline and the reference arm)
+
+def oracle_sample_run(workload: dict, scale: int):
+    import oracle as orc
+
+    g = workload["sample"](scale)
+    units = 0
+    t0 = time.perf_counter()
+    for r, s in workload["rs"]:
+        d = orc.decompose(g, r, s)
+        units += units_of(r, s, d.n_s)
+    dt = time.perf_counter() - t0
+    return units, dt, g
+
+
+def pick_sample_scale(per_step_budget_s: float) -> int:
+    # one-core oracle times on this R-MAT family: scale 12 ~ 27 s, scale 11 ~ 9 s, scale 10 ~ 3 s
+    if per_step_budget_s >= 30:
+        return 12
+    if per_step_budget_s >= 10:
+        return 11
+    return 10
+
+
+def run_reference(args, world, rank):
+    """--impl reference: the CPU oracle, as it stands, on a bounded sample per step."""
+    if rank != 0:
+        return 0
+    wl = WORKLOADS[args.workload]
+    steps, warm = args.steps, args.warmup
+    scale = pick_sample_scale(150.0 / max(1, steps + warm))
+    for _ in range(warm):
+        oracle_sample_run(wl, scale)
+    tot_units, tot_t = 0, 0.0
+    g = None
+    for _ in range(steps):
+        u, dt, g = oracle_sample_run(wl, scale)
+        tot_units += u
+        tot_t += dt
+    value = tot_units / tot_t
+    sample = wl["sample_desc"].format(scale=scale) + f": n={g.n}, m={g.m}"
+    line = {"impl": "reference", "metric": "(r,s) s-cliques/sec", "value": value, "unit": "s-cliques/s",
+            "n_gpus": args.gpus, "steps": steps, "warmup": warm, "ms_per_step": 1000.0 * tot_t / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "config": {"workload": args.workload, "desc": wl["desc"]},
+            "cpu_baseline": {"value": value, "unit": "s-cliques/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "s-cliques/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------------
+# our arm
+
+def main():
+    args = parse_args()
+    world, rank, local, pg = dist_setup(want_nccl=(args.impl == "ours"))
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import numpy as np
+    import torch
+
+    import paper_2111_10980_gb300 as nd
+
+    torch.cuda.set_device(local)
+    wl = WORKLOADS[args.workload]
+    width = wl.get("width", 0)
+    g = wl["gen"]()
+    stream = torch.cuda.Stream(device=local)
+    ctx = nd.nd_ctx_create(local, stream=stream)
+    rp_d = torch.from_numpy(g.rowptr).to(f"cuda:{local}")
+    col_d = torch.from_numpy(g.col).to(f"cuda:{local}")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=f"cuda:{local}")
+    torch.cuda.synchronize()
+    G = nd.nd_load_csr(ctx, rp_d, col_d)
+
+    outs = {}
+
+    def step():
+        nd.nd_graph_reset(G)  # every step rebuilds orientation and indexes
+        stats = {}
+        for r, s in wl["rs"]:
+            core = outs.get((r, s))
+            if core is None:  # first warm-up step: learn n_r, then keep a device output buffer
+                _, _, st = nd.nd_decompose(G, r, s, count_width=width, want_round=False)
+                outs[(r, s)] = torch.empty(max(st["n_r"], 1), dtype=torch.int32, device=f"cuda:{local}")
+            else:
+                _, _, st = nd.nd_decompose(G, r, s, count_width=width, core_out=core, want_round=False)
+            stats[(r, s)] = st
+        return stats
+
+    for _ in range(max(args.warmup, 1)):
+        stats = step()
+
+    # timed region
+    sampler = ClockSampler(gpu_uuid(local))
+    barrier(pg, local)
+    torch.cuda.synchronize()
+    sampler.start()
+    launches0 = nd.nd_kernel_launches()
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    per_step_stats = []
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)  # evict the previous step's data from L2 (not timed)
+        with torch.cuda.stream(stream):
+            ev0[i].record(stream)
+            per_step_stats.append(step())
+            ev1[i].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    launches = nd.nd_kernel_launches() - launches0
+    clocks = sampler.stop()
+    barrier(pg, local)
+    t_ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
+    t_ms = max_over_ranks(pg, t_ms, local)
+
+    stats = per_step_stats[-1]
+    units_per_step = sum(units_of(r, s, stats[(r, s)]["n_s"]) for r, s in wl["rs"])
+    rcl_per_step = sum(stats[(r, s)]["n_r"] for r, s in wl["rs"])
+    value = units_per_step * args.steps * world / (t_ms / 1000.0)
+    peel_ms = [sum(st[(r, s)]["t_peel_ms"] for r, s in wl["rs"]) for st in per_step_stats]
+    peeled_per_s = rcl_per_step * args.steps * world / (sum(peel_ms) / 1000.0)
+
+    # roofline of the dominant kernel: the (r,s) = (3,4) counting kernel when present, else the
+    # (2,3) one; algorithmic bytes = the index entries every r-clique must read plus the matched
+    # list entries ("Roofline")
+    roof = roofline(wl, per_step_stats, g)
+
+    line = {"metric": "(r,s) s-cliques/sec", "value": value, "unit": "s-cliques/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int64" if width == 8 else "int32", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": wl["desc"], "n": g.n, "m": g.m,
+                       "rs": [f"({r},{s})" for r, s in wl["rs"]], "parallelism": f"replicas x{world}",
+                       "l2": "flushed between steps (256 MiB write, outside the step events)"},
+            "r_cliques_peeled_per_s": peeled_per_s,
+            "wall_s_timed": wall,
+            "per_rs": {f"({r},{s})": {k: stats[(r, s)][k] for k in
+                                      ("n_r", "n_s", "rho", "max_core", "listed", "advances", "refills",
+                                       "count_width", "t_orient_ms", "t_index_ms", "t_count_ms", "t_peel_ms",
+                                       "t_total_ms")} for r, s in wl["rs"]},
+            "gpu_launches": launches,
+            "roofline": roof,
+            "clocks": clocks}
+
+    # end to end through the C ABI with pinned host buffers (H2D of the CSR, D2H of every core array)
+    if not args.no_e2e:
+        line["e2e"] = e2e(nd, wl, g, local, width, args.e2e_steps, world, pg)
+
+    nd.nd_graph_free(G)
+    nd.nd_ctx_destroy(ctx)
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        scale = 12 if args.workload == "rmat20" else 14
+        units, dt, sg = oracle_sample_run(wl, scale)
+        line["cpu_baseline"] = {"value": units / dt, "unit": "s-cliques/s", "cores": 1, "kind": "oracle",
+                                "sample": wl["sample_desc"].format(scale=scale) + f": n={sg.n}, m={sg.m}, "
+                                f"{dt:.1f} s single-threaded"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+    return 0
+
+
+def roofline(wl, per_step_stats, g):
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = peaks.get("hbm_gbs")
+    src = "measured"
+    if not peak:
+        peak, src = 6800.0, "fallback"
+    rs = (3, 4) if (3, 4) in wl["rs"] else wl["rs"][0]
+    r, s = rs
+    ts = [st[rs]["t_count_ms"] for st in per_step_stats]
+    st = per_step_stats[-1][rs]
+    n_r, n_s = st["n_r"], st["n_s"]
+    if rs == (3, 4):
+        # per triangle: 3 edge ids (12 B) + 3 list bounds (48 B) + the count (4 B); per (triangle,
+        # common neighbour) pair the entry in each of the three lists (12 B); sum of counts = 4 n_4
+        alg = 64 * n_r + 12 * 4 * n_s
+        kernel = "k_count34"
+    elif rs == (2, 3):
+        # per edge: endpoints (8 B) + 2 row bounds (32 B) + count (4 B); per (edge, common
+        # neighbour) the entry in both rows (8 B); sum of counts = 3 n_3
+        alg = 44 * n_r + 8 * 3 * n_s
+        kernel = "k_count23"
+    else:
+        alg = 0
+        kernel = "k_count%d%d" % rs
+    t = statistics.mean(ts) / 1000.0
+    achieved = alg / t / 1e9 if t > 0 else 0.0
+    return {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None, "peak_source": src,
+            "algorithmic_bytes_per_launch": alg, "avg_launch_ms": t * 1000.0}
+
+
+def e2e(nd, wl, g, local, width, steps, world, pg):
+    import numpy as np
+    import torch
+
+    rp_h = torch.from_numpy(g.rowptr).pin_memory()
+    col_h = torch.from_numpy(g.col).pin_memory()
+    stream = torch.cuda.Stream(device=local)
+    ctx = nd.nd_ctx_create(local, stream=stream)
+    outs = {}
+    h2d = rp_h.numel() * 8 + col_h.numel() * 4
+    d2h = 0
+    units = 0
+
+    def one():
+        nonlocal d2h, units
+        G = nd.nd_load_csr(ctx, rp_h, col_h)
+        d2h = 0
+        units = 0
+        for r, s in wl["rs"]:
+            core = outs.get((r, s))
+            if core is None:
+                _, _, st = nd.nd_decompose(G, r, s, count_width=width, want_round=False)
+                outs[(r, s)] = torch.empty(st["n_r"], dtype=torch.int32).pin_memory()
+                core = outs[(r, s)]
+            _, _, st = nd.nd_decompose(G, r, s, count_width=width, core_out=core, want_round=False)
+            d2h += 4 * st["n_r"]
+            units += units_of(r, s, st["n_s"])
+        nd.nd_graph_free(G)
+
+    one()  # warm-up (allocations, first-touch of pinned outputs)
+    torch.cuda.synchronize()
+    barrier(pg, local)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    dt = max_over_ranks(pg, dt, local)
+    nd.nd_ctx_destroy(ctx)
+    return {"value": units * steps * world / dt, "unit": "s-cliques/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "steps": steps}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,183 @@
+/*
+ * nd.h -- C ABI of the GB300 (sm_103a) (r,s) nucleus decomposition library (libnd.so).
+ *
+ * The library computes, for every r-clique R of a simple undirected graph, its
+ * (r,s)-clique core number: the largest c such that R lies in a c-(r,s) nucleus, i.e. in a
+ * maximal set of r-cliques each of which is contained in at least c s-cliques whose
+ * r-subsets all belong to the set (Shi, Dhulipala, Shun, "Theoretically and Practically
+ * Efficient Parallel Nucleus Decomposition", Section 2, definition of the (r,s) nucleus
+ * decomposition problem; the connectivity condition of the original definition is not
+ * imposed, as in the paper). (1,2) is k-core coreness; (2,3) is k-truss trussness minus 2.
+ *
+ * Every step runs in hand-written CUDA kernels on one GPU: degree orientation (Section 3,
+ * O(alpha)-orientation), the r-clique index (Section 5.2-5.3), s-clique counting
+ * (Algorithm 1 with Count-Func of Algorithm 2), and the peeling loop of Algorithm 2 (bucket
+ * extraction, Update/Update-Func with exact integer decrements). There is no CPU fallback.
+ *
+ * Conventions shared by all calls
+ *   - Every call returns an int status (ND_OK on success). On failure nothing visible to the
+ *     caller has been written except where stated, and nd_last_error() describes the error.
+ *   - Graph input is a symmetric CSR: rowptr int64[n+1] (rowptr[0] = 0), col int32[rowptr[n]],
+ *     every neighbour list sorted ascending, no self-loops, no duplicate entries, and (u,v)
+ *     present iff (v,u) is. ND_VALIDATE checks all of this on the GPU (ND_EINVAL otherwise).
+ *   - Pointer arguments are host memory unless ND_PTR_DEVICE is passed in flags, in which
+ *     case they are device memory on the context's device. The library never keeps a
+ *     caller's pointer after a call returns (except nd_submit, see there); it copies inputs.
+ *   - Canonical r-clique order (the id space of all per-r-clique outputs): r-cliques sorted
+ *     lexicographically by their ascending tuple of vertex ids. r = 1: vertex id; r = 2:
+ *     edges (u < v) in CSR order; r = 3: triangles (a < b < c) by (a, b, c).
+ *   - Supported (r, s): (1,2), (1,3), (2,3), (2,4), (3,4). Others return ND_EINVAL.
+ *   - All work is issued on the context's stream; synchronous calls synchronise that stream
+ *     before returning.
+ */
+#ifndef ND_H
+#define ND_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define ND_API __attribute__((visibility("default")))
+#else
+#define ND_API
+#endif
+
+/* ---- status codes ------------------------------------------------------------------- */
+#define ND_OK 0
+#define ND_EINVAL 1     /* bad argument, unsupported (r,s), or malformed CSR (ND_VALIDATE) */
+#define ND_ENOMEM 2     /* device allocation failed or the context's memory budget is exceeded */
+#define ND_EOVERFLOW 3  /* a count exceeds the chosen width, or an id space exceeds int32 */
+#define ND_ETIMEOUT 4   /* the device-side peeling loop hit its round cap */
+#define ND_EBUSY 5      /* server has no free slot / request queue full */
+#define ND_PENDING 6    /* nd_poll: the request is still running */
+#define ND_EINTERNAL 7  /* internal inconsistency detected on the device */
+#define ND_ECUDA 8      /* a CUDA runtime call failed */
+
+/* ---- flags --------------------------------------------------------------------------- */
+#define ND_PTR_DEVICE 0x1 /* pointer arguments are device memory (default: host memory) */
+#define ND_VALIDATE 0x2   /* nd_load_csr: check the CSR invariants on the GPU */
+#define ND_NO_GRAPH 0x4   /* nd_decompose: launch the peeling rounds one by one, no CUDA graph */
+
+/* ---- orientation modes (nd_orient) --------------------------------------------------- */
+#define ND_ORIENT_DEGREE 0     /* rank by (degree, id); out-degree <= sqrt(2m) */
+#define ND_ORIENT_DEGENERACY 1 /* rank by (k-core peeling round, id); out-degree <= degeneracy */
+
+typedef struct nd_ctx nd_ctx;
+typedef struct nd_graph nd_graph;
+
+/* Device allocator hooks: alloc returns device memory of at least `bytes` bytes usable on
+ * `stream` (NULL on failure); free releases it. `user` is passed through. */
+typedef void *(*nd_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*nd_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
+
+/* Statistics of one decomposition (all times in milliseconds, measured with CUDA events on
+ * the context's stream). */
+typedef struct nd_stats {
+    int64_t n_r;        /* number of r-cliques */
+    int64_t n_s;        /* number of s-cliques */
+    int64_t rho;        /* peeling rounds: each round peels every unpeeled r-clique whose count
+                           is <= k, after k = max(k, minimum unpeeled count) */
+    int64_t max_core;   /* largest core number */
+    int64_t listed;     /* (s-clique, peeled member) pairs re-listed by Update over the run */
+    int64_t advances;   /* rounds that moved to a new level k */
+    int64_t refills;    /* bucket-window rebuilds */
+    int32_t count_width;/* 4 or 8: bytes per count used on the device */
+    int32_t orient_mode;
+    double t_orient_ms; /* orientation (and the r = 1, 2 index) */
+    double t_index_ms;  /* r = 3 index */
+    double t_count_ms;  /* s-clique counting */
+    double t_peel_ms;   /* the peeling loop */
+    double t_total_ms;
+} nd_stats;
+
+/* ---- context ------------------------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`. `stream` is a cudaStream_t to issue all work on
+ * (NULL: the library creates and owns a non-blocking stream). `mem_budget` caps the device
+ * bytes the context may hold at once (0: no cap). *out receives the handle.
+ * Errors: ND_EINVAL (out NULL, bad device), ND_ECUDA. */
+ND_API int nd_ctx_create(int device, void *stream, size_t mem_budget, nd_ctx **out);
+
+/* Route the context's device allocations through caller hooks (e.g. a framework's caching
+ * allocator). Must be called before any graph is loaded. Pass NULLs to restore the default
+ * (cudaMallocAsync on the context's stream). Errors: ND_EINVAL, ND_EBUSY (graphs exist). */
+ND_API int nd_ctx_set_allocator(nd_ctx *ctx, nd_alloc_fn alloc, nd_free_fn free_fn, void *user);
+
+/* Destroy a context. All graphs created from it must have been freed (ND_EBUSY otherwise). */
+ND_API int nd_ctx_destroy(nd_ctx *ctx);
+
+/* Device bytes currently held by the context (0 for a NULL context). */
+ND_API size_t nd_ctx_bytes_in_use(const nd_ctx *ctx);
+
+/* Number of CUDA kernels this process has launched through the library so far (every node of
+ * a replayed CUDA graph counts once per replay). */
+ND_API int64_t nd_kernel_launches(void);
+
+/* Human-readable description of the last error raised on the calling thread ("" if none).
+ * The string stays valid until the next nd_* call on the same thread. */
+ND_API const char *nd_last_error(void);
+
+/* ---- graphs -------------------------------------------------------------------------- */
+
+/* Copy a symmetric CSR graph (see conventions) to the device. n >= 0; rowptr int64[n+1];
+ * col int32[rowptr[n]]. flags: ND_PTR_DEVICE, ND_VALIDATE. The caller keeps ownership of
+ * its arrays. Errors: ND_EINVAL (bad sizes; malformed CSR with ND_VALIDATE), ND_ENOMEM,
+ * ND_EOVERFLOW (more than 2^31 - 1 undirected edges). */
+ND_API int nd_load_csr(nd_ctx *ctx, int32_t n, const int64_t *rowptr, const int32_t *col, int flags, nd_graph **out);
+
+/* Free a graph and every device structure derived from it. NULL is accepted. */
+ND_API int nd_graph_free(nd_graph *g);
+
+/* Number of vertices and undirected edges of a loaded graph. */
+ND_API int nd_graph_size(const nd_graph *g, int32_t *n, int64_t *m);
+
+/* Orient the graph (Section 3, O(alpha)-orientation; Algorithm 2 line "Orient"): every edge
+ * is directed from the lower to the higher vertex in a total order; mode selects the order
+ * (ND_ORIENT_DEGREE or ND_ORIENT_DEGENERACY). Also builds the canonical edge index. Calling
+ * it again with the same mode does nothing; another mode rebuilds the orientation. Vertex
+ * ids are never changed: all outputs use the caller's ids. nd_count / nd_decompose orient
+ * with ND_ORIENT_DEGREE if the graph is not oriented yet. Errors: ND_EINVAL, ND_ENOMEM. */
+ND_API int nd_orient(nd_graph *g, int mode);
+
+/* Discard the orientation and every derived index (the next call rebuilds them). */
+ND_API int nd_graph_reset(nd_graph *g);
+
+/* s-clique counts per r-clique (Algorithm 2, Count-Func over all s-cliques listed by
+ * Algorithm 1). count_width: 4 (int32), 8 (int64) or 0 (4 if no count can exceed 2^31-1,
+ * else 8). counts_out: NULL, or n_r values of count_width bytes in canonical order (host,
+ * or device with ND_PTR_DEVICE). n_r_out / n_s_out (nullable, host) receive the numbers
+ * of r- and s-cliques. To size counts_out, call first with counts_out = NULL.
+ * Errors: ND_EINVAL, ND_ENOMEM, ND_EOVERFLOW (a count exceeds width 4 when width 4 was
+ * asked for, or n_r >= 2^31). */
+ND_API int nd_count(nd_graph *g, int r, int s, int count_width, void *counts_out, int flags, int64_t *n_r_out,
+             int64_t *n_s_out);
+
+/* (r,s) nucleus decomposition (Algorithm 2): core_out receives the core number of every
+ * r-clique (int32[n_r], canonical order); round_out (nullable) the peeling round in which
+ * each r-clique was removed (int32[n_r], rounds numbered from 0); st (nullable, host) the
+ * statistics. Pointers are host memory unless flags has ND_PTR_DEVICE. core_out may be NULL
+ * (only the statistics are produced). count_width as in nd_count.
+ * Errors: ND_EINVAL, ND_ENOMEM, ND_EOVERFLOW, ND_ETIMEOUT (round cap), ND_EINTERNAL. */
+ND_API int nd_decompose(nd_graph *g, int r, int s, int count_width, int32_t *core_out, int32_t *round_out, int flags,
+                 nd_stats *st);
+
+/* Per-round record of the last nd_decompose on this graph: sizes_out[t] = |A| peeled in
+ * round t, levels_out[t] = level k of round t, for t < min(rho, cap). Host pointers.
+ * *rho_out receives rho. Rounds past the device-side record limit (2^22) are not recorded.
+ * Errors: ND_EINVAL (no decomposition yet). */
+ND_API int nd_rounds(nd_graph *g, int64_t *sizes_out, int64_t *levels_out, int64_t cap, int64_t *rho_out);
+
+/* The r-cliques themselves (the inverse index map, Section 5.3): tuples_out receives n_r
+ * ascending tuples of r int32 vertex ids in canonical order (host, or device with
+ * ND_PTR_DEVICE; NULL to query n_r only). r in {1, 2, 3}. Errors: ND_EINVAL, ND_ENOMEM. */
+ND_API int nd_rcliques(nd_graph *g, int r, int32_t *tuples_out, int flags, int64_t *n_r_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ND_H */

@@ -1,0 +1,297 @@
+"""Python binding of libnd.so, the GB300 (sm_103a) (r,s) nucleus decomposition library.
+
+Argument marshalling only: every function below calls the C entry point of the same name in
+``include/nd.h`` through ctypes; all computation happens in the library's CUDA kernels. If
+the library cannot be loaded, every call raises -- there is no CPU fallback.
+
+Arrays may be numpy arrays (host memory) or torch CUDA tensors (device memory; the
+ND_PTR_DEVICE flag is set automatically). Typical use::
+
+    import paper_2111_10980_gb300 as nd
+    ctx = nd.nd_ctx_create(0)
+    g = nd.nd_load_csr(ctx, rowptr, col)          # int64[n+1], int32[2m]
+    core, rnd, st = nd.nd_decompose(g, 2, 3)      # k-truss numbers (trussness - 2)
+    nd.nd_graph_free(g); nd.nd_ctx_destroy(ctx)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(_PKG, "libnd.so")
+
+ND_OK, ND_EINVAL, ND_ENOMEM, ND_EOVERFLOW, ND_ETIMEOUT, ND_EBUSY, ND_PENDING, ND_EINTERNAL, ND_ECUDA = range(9)
+ND_PTR_DEVICE = 0x1
+ND_VALIDATE = 0x2
+ND_NO_GRAPH = 0x4
+ND_ORIENT_DEGREE = 0
+ND_ORIENT_DEGENERACY = 1
+STATUS_NAMES = {0: "ND_OK", 1: "ND_EINVAL", 2: "ND_ENOMEM", 3: "ND_EOVERFLOW", 4: "ND_ETIMEOUT", 5: "ND_EBUSY",
+                6: "ND_PENDING", 7: "ND_EINTERNAL", 8: "ND_ECUDA"}
+
+# every entry point declared in include/nd.h
+API = ["nd_ctx_create", "nd_ctx_set_allocator", "nd_ctx_destroy", "nd_ctx_bytes_in_use", "nd_kernel_launches", "nd_last_error",
+       "nd_load_csr", "nd_graph_free", "nd_graph_size", "nd_orient", "nd_graph_reset", "nd_count", "nd_decompose",
+       "nd_rounds", "nd_rcliques"]
+
+
+class NdError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {message}")
+        self.code = code
+
+
+class nd_stats(ctypes.Structure):
+    _fields_ = [("n_r", ctypes.c_int64), ("n_s", ctypes.c_int64), ("rho", ctypes.c_int64),
+                ("max_core", ctypes.c_int64), ("listed", ctypes.c_int64), ("advances", ctypes.c_int64),
+                ("refills", ctypes.c_int64), ("count_width", ctypes.c_int32), ("orient_mode", ctypes.c_int32),
+                ("t_orient_ms", ctypes.c_double), ("t_index_ms", ctypes.c_double), ("t_count_ms", ctypes.c_double),
+                ("t_peel_ms", ctypes.c_double), ("t_total_ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libnd.so (building it first with nvcc if it is missing). Raises if it cannot be
+    built or loaded: the binding never substitutes another implementation."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIBPATH):
+            from . import build as _b
+            _b.build()
+        L = ctypes.CDLL(LIBPATH)
+        vp, i32, i64, i32p, i64p = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(
+            ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)
+        L.nd_ctx_create.argtypes = [ctypes.c_int, vp, ctypes.c_size_t, ctypes.POINTER(vp)]
+        L.nd_ctx_set_allocator.argtypes = [vp, ALLOC_FN, FREE_FN, vp]
+        L.nd_ctx_destroy.argtypes = [vp]
+        L.nd_ctx_bytes_in_use.argtypes = [vp]
+        L.nd_ctx_bytes_in_use.restype = ctypes.c_size_t
+        L.nd_kernel_launches.argtypes = []
+        L.nd_kernel_launches.restype = ctypes.c_int64
+        L.nd_last_error.argtypes = []
+        L.nd_last_error.restype = ctypes.c_char_p
+        L.nd_load_csr.argtypes = [vp, i32, vp, vp, ctypes.c_int, ctypes.POINTER(vp)]
+        L.nd_graph_free.argtypes = [vp]
+        L.nd_graph_size.argtypes = [vp, i32p, i64p]
+        L.nd_orient.argtypes = [vp, ctypes.c_int]
+        L.nd_graph_reset.argtypes = [vp]
+        L.nd_count.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, i64p, i64p]
+        L.nd_decompose.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_int,
+                                   ctypes.POINTER(nd_stats)]
+        L.nd_rounds.argtypes = [vp, vp, vp, i64, i64p]
+        L.nd_rcliques.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, i64p]
+        for name in API:
+            if name not in ("nd_ctx_bytes_in_use", "nd_last_error", "nd_kernel_launches"):
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+        return L
+
+
+def _check(rc: int):
+    if rc != ND_OK:
+        msg = lib().nd_last_error()
+        raise NdError(rc, msg.decode() if msg else "")
+
+
+def _is_torch_cuda(a) -> bool:
+    return hasattr(a, "is_cuda") and hasattr(a, "data_ptr") and bool(a.is_cuda)
+
+
+def _ptr(a):
+    """(address, is_device) of a numpy array or torch tensor (None -> (None, False))."""
+    if a is None:
+        return None, False
+    if _is_torch_cuda(a):
+        if not a.is_contiguous():
+            raise ValueError("device tensors must be contiguous")
+        return ctypes.c_void_p(a.data_ptr()), True
+    if hasattr(a, "data_ptr"):  # torch CPU tensor
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return ctypes.c_void_p(a.data_ptr()), False
+    if not isinstance(a, np.ndarray) or not a.flags.c_contiguous:
+        raise ValueError("host arrays must be C-contiguous numpy arrays")
+    return ctypes.c_void_p(a.ctypes.data), False
+
+
+class Handle:
+    """An opaque library handle (context or graph)."""
+
+    def __init__(self, ptr: ctypes.c_void_p, kind: str, owner=None):
+        self.ptr = ptr
+        self.kind = kind
+        self.owner = owner
+        self.hooks = None
+
+    @property
+    def value(self):
+        return self.ptr
+
+
+def nd_ctx_create(device: int = 0, stream=None, mem_budget: int = 0) -> Handle:
+    """Create a context (nd.h: nd_ctx_create). ``stream`` is a torch.cuda.Stream, a raw
+    cudaStream_t integer, or None (the library makes its own)."""
+    raw = None
+    if stream is not None:
+        raw = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    out = ctypes.c_void_p()
+    _check(lib().nd_ctx_create(int(device), raw, ctypes.c_size_t(int(mem_budget)), ctypes.byref(out)))
+    return Handle(out, "ctx")
+
+
+def nd_ctx_set_allocator(ctx: Handle, alloc, free):
+    """Route device allocations through Python callables alloc(bytes, stream) -> int address
+    and free(address, bytes, stream) (nd.h: nd_ctx_set_allocator). None restores the default."""
+    if alloc is None:
+        _check(lib().nd_ctx_set_allocator(ctx.ptr, ALLOC_FN(), FREE_FN(), None))
+        ctx.hooks = None
+        return
+    a = ALLOC_FN(lambda nbytes, stream, user: int(alloc(int(nbytes), stream)) or None)
+    f = FREE_FN(lambda p, nbytes, stream, user: free(int(p), int(nbytes), stream))
+    _check(lib().nd_ctx_set_allocator(ctx.ptr, a, f, None))
+    ctx.hooks = (a, f)  # keep the trampolines alive
+
+
+def torch_allocator_hooks(device: int = 0):
+    """(alloc, free) callables that take device memory from PyTorch's caching allocator."""
+    import torch
+
+    def alloc(nbytes, stream):
+        return torch.cuda.caching_allocator_alloc(nbytes, device, stream)
+
+    def free(p, nbytes, stream):
+        torch.cuda.caching_allocator_delete(p)
+
+    return alloc, free
+
+
+def nd_ctx_destroy(ctx: Handle):
+    _check(lib().nd_ctx_destroy(ctx.ptr))
+    ctx.ptr = None
+
+
+def nd_ctx_bytes_in_use(ctx: Handle) -> int:
+    return int(lib().nd_ctx_bytes_in_use(ctx.ptr))
+
+
+def nd_kernel_launches() -> int:
+    """Kernels launched by the library in this process so far (nd.h: nd_kernel_launches)."""
+    return int(lib().nd_kernel_launches())
+
+
+def nd_last_error() -> str:
+    m = lib().nd_last_error()
+    return m.decode() if m else ""
+
+
+def nd_load_csr(ctx: Handle, rowptr, col, flags: int = 0) -> Handle:
+    """Copy a symmetric CSR graph to the device (nd.h: nd_load_csr)."""
+    p_rp, d_rp = _ptr(rowptr)
+    p_col, d_col = _ptr(col)
+    if d_rp != d_col:
+        raise ValueError("rowptr and col must both be host or both be device arrays")
+    n = int(rowptr.shape[0]) - 1
+    if str(rowptr.dtype).split(".")[-1] != "int64" or str(col.dtype).split(".")[-1] != "int32":
+        raise ValueError("rowptr must be int64 and col int32")
+    out = ctypes.c_void_p()
+    _check(lib().nd_load_csr(ctx.ptr, n, p_rp, p_col, int(flags) | (ND_PTR_DEVICE if d_rp else 0),
+                             ctypes.byref(out)))
+    return Handle(out, "graph", ctx)
+
+
+def nd_graph_free(g: Handle):
+    if g is not None and g.ptr is not None:
+        _check(lib().nd_graph_free(g.ptr))
+        g.ptr = None
+
+
+def nd_graph_size(g: Handle):
+    n = ctypes.c_int32()
+    m = ctypes.c_int64()
+    _check(lib().nd_graph_size(g.ptr, ctypes.byref(n), ctypes.byref(m)))
+    return n.value, m.value
+
+
+def nd_orient(g: Handle, mode: int = ND_ORIENT_DEGREE):
+    _check(lib().nd_orient(g.ptr, int(mode)))
+
+
+def nd_graph_reset(g: Handle):
+    _check(lib().nd_graph_reset(g.ptr))
+
+
+def nd_count(g: Handle, r: int, s: int, count_width: int = 0, out=None):
+    """s-clique counts per r-clique (nd.h: nd_count). Returns (counts, n_r, n_s); counts is
+    ``out`` if given (host numpy or device tensor of the right width), else a new numpy array."""
+    n_r = ctypes.c_int64()
+    n_s = ctypes.c_int64()
+    _check(lib().nd_count(g.ptr, r, s, count_width, None, 0, ctypes.byref(n_r), None))
+    width = count_width
+    if out is None:
+        if width == 0:
+            width = 8  # a host int64 array holds every width; ask the library for 8 bytes
+        out = np.zeros(n_r.value, dtype=np.int64 if width == 8 else np.int32)
+    else:
+        width = out.element_size() if hasattr(out, "element_size") else out.itemsize
+    p, dev = _ptr(out)
+    _check(lib().nd_count(g.ptr, r, s, width, p, ND_PTR_DEVICE if dev else 0, ctypes.byref(n_r),
+                          ctypes.byref(n_s)))
+    return out, n_r.value, n_s.value
+
+
+def nd_decompose(g: Handle, r: int, s: int, count_width: int = 0, core_out=None, round_out=None,
+                 flags: int = 0, want_round: bool = True):
+    """(r,s) nucleus decomposition (nd.h: nd_decompose). Returns (core, round, stats dict).
+    With device tensors for core_out/round_out the results stay on the device."""
+    if core_out is None:
+        n_r = ctypes.c_int64()
+        _check(lib().nd_count(g.ptr, r, s, count_width, None, 0, ctypes.byref(n_r), None))
+        core_out = np.zeros(n_r.value, np.int32)
+        if want_round and round_out is None:
+            round_out = np.zeros(n_r.value, np.int32)
+    pc, dc = _ptr(core_out)
+    pr, dr = _ptr(round_out)
+    if round_out is not None and dc != dr:
+        raise ValueError("core_out and round_out must live in the same memory")
+    st = nd_stats()
+    _check(lib().nd_decompose(g.ptr, r, s, count_width, pc, pr, int(flags) | (ND_PTR_DEVICE if dc else 0),
+                              ctypes.byref(st)))
+    return core_out, round_out, st.as_dict()
+
+
+def nd_rounds(g: Handle, cap: int | None = None):
+    """(sizes, levels, rho) of the last decomposition on g (nd.h: nd_rounds)."""
+    rho = ctypes.c_int64()
+    _check(lib().nd_rounds(g.ptr, None, None, 0, ctypes.byref(rho)))
+    k = rho.value if cap is None else min(cap, rho.value)
+    sizes = np.zeros(max(k, 1), np.int64)
+    levels = np.zeros(max(k, 1), np.int64)
+    _check(lib().nd_rounds(g.ptr, ctypes.c_void_p(sizes.ctypes.data), ctypes.c_void_p(levels.ctypes.data), k,
+                           ctypes.byref(rho)))
+    return sizes[:k], levels[:k], rho.value
+
+
+def nd_rcliques(g: Handle, r: int, out=None):
+    """The r-cliques as ascending tuples in canonical order (nd.h: nd_rcliques)."""
+    n_r = ctypes.c_int64()
+    _check(lib().nd_rcliques(g.ptr, r, None, 0, ctypes.byref(n_r)))
+    if out is None:
+        out = np.zeros((n_r.value, r), np.int32)
+    p, dev = _ptr(out)
+    _check(lib().nd_rcliques(g.ptr, r, p, ND_PTR_DEVICE if dev else 0, ctypes.byref(n_r)))
+    return out

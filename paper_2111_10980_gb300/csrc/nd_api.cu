@@ -1,0 +1,851 @@
+// C ABI of libnd.so (declared in include/nd.h): contexts, device memory, graph lifecycle and
+// the host-side sequencing of Algorithm 2 (orient, index, count, peel). Every arithmetic step
+// runs in the kernels of nd_graph.cu, nd_count.cu and nd_peel.cu; this file only allocates,
+// launches and copies.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <climits>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "nd.h"
+#include "nd_common.cuh"
+#include "nd_host.h"
+
+// ------------------------------------------------------------------------------------
+// errors
+
+static thread_local std::string g_last_error;
+
+int nd_set_error(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+extern "C" const char* nd_last_error(void) { return g_last_error.c_str(); }
+
+// ------------------------------------------------------------------------------------
+// memory
+
+int nd_alloc(nd_ctx* ctx, DBuf& b, size_t bytes) {
+    nd_free(ctx, b);
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (ctx->budget && ctx->in_use.load() + bytes > ctx->budget)
+        return nd_set_error(ND_ENOMEM, "memory budget exceeded: %zu + %zu > %zu bytes", ctx->in_use.load(), bytes,
+                            ctx->budget);
+    void* p = nullptr;
+    if (ctx->af) {
+        p = ctx->af(bytes, (void*)ctx->stream, ctx->user);
+        if (!p) return nd_set_error(ND_ENOMEM, "allocator hook failed for %zu bytes", bytes);
+    } else {
+        cudaError_t e = cudaMallocAsync(&p, bytes, ctx->stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return nd_set_error(ND_ENOMEM, "cudaMallocAsync(%zu): %s", bytes, cudaGetErrorString(e));
+        }
+    }
+    b.p = p;
+    b.bytes = bytes;
+    ctx->in_use += bytes;
+    return ND_OK;
+}
+
+void nd_free(nd_ctx* ctx, DBuf& b) {
+    if (!b.p) return;
+    if (ctx->ff)
+        ctx->ff(b.p, b.bytes, (void*)ctx->stream, ctx->user);
+    else
+        cudaFreeAsync(b.p, ctx->stream);
+    ctx->in_use -= b.bytes;
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+#define ND_TRY(x)                       \
+    do {                                \
+        int _rc = (x);                  \
+        if (_rc != ND_OK) return _rc;   \
+    } while (0)
+
+#define ND_CUDA(x)                                                                          \
+    do {                                                                                    \
+        cudaError_t _e = (x);                                                               \
+        if (_e != cudaSuccess) {                                                            \
+            cudaGetLastError();                                                             \
+            return nd_set_error(ND_ECUDA, "%s failed: %s", #x, cudaGetErrorString(_e));     \
+        }                                                                                   \
+    } while (0)
+
+int nd_check_launch(const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return nd_set_error(ND_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+    return ND_OK;
+}
+
+int nd_sync(nd_ctx* ctx, const char* what) {
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return nd_set_error(ND_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+    }
+    return ND_OK;
+}
+
+// device scalar helpers: a small per-graph scratch holds flags and reduction results
+static int scalar_zero(nd_graph* g) {
+    ND_CUDA(cudaMemsetAsync(g->scal.p, 0, g->scal.bytes, g->ctx->stream));
+    return ND_OK;
+}
+
+template <typename T>
+static int read_back(nd_graph* g, const void* dptr, T* out, const char* what) {
+    ND_CUDA(cudaMemcpyAsync(g->ctx->pinned, dptr, sizeof(T), cudaMemcpyDeviceToHost, g->ctx->stream));
+    ND_TRY(nd_sync(g->ctx, what));
+    memcpy(out, g->ctx->pinned, sizeof(T));
+    return ND_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// context
+
+extern "C" int nd_ctx_create(int device, void* stream, size_t mem_budget, nd_ctx** out) {
+    if (!out) return nd_set_error(ND_EINVAL, "nd_ctx_create: out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    ND_CUDA(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return nd_set_error(ND_EINVAL, "nd_ctx_create: no CUDA device %d", device);
+    ND_CUDA(cudaSetDevice(device));
+    nd_ctx* c = new nd_ctx();
+    c->device = device;
+    c->budget = mem_budget;
+    if (stream) {
+        c->stream = (cudaStream_t)stream;
+        c->own_stream = false;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete c;
+            cudaGetLastError();
+            return nd_set_error(ND_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+        }
+        c->own_stream = true;
+    }
+    // keep freed blocks in the device's default pool instead of returning them to the driver
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+    if (cudaMallocHost(&c->pinned, 4096) != cudaSuccess) {
+        cudaGetLastError();
+        if (c->own_stream) cudaStreamDestroy(c->stream);
+        delete c;
+        return nd_set_error(ND_ECUDA, "cudaMallocHost failed");
+    }
+    *out = c;
+    return ND_OK;
+}
+
+extern "C" int nd_ctx_set_allocator(nd_ctx* ctx, nd_alloc_fn alloc, nd_free_fn free_fn, void* user) {
+    if (!ctx) return nd_set_error(ND_EINVAL, "nd_ctx_set_allocator: NULL context");
+    if ((alloc == nullptr) != (free_fn == nullptr))
+        return nd_set_error(ND_EINVAL, "nd_ctx_set_allocator: give both hooks or neither");
+    if (ctx->ngraphs.load() > 0) return nd_set_error(ND_EBUSY, "nd_ctx_set_allocator: graphs are still loaded");
+    ctx->af = alloc;
+    ctx->ff = free_fn;
+    ctx->user = user;
+    return ND_OK;
+}
+
+extern "C" int nd_ctx_destroy(nd_ctx* ctx) {
+    if (!ctx) return ND_OK;
+    if (ctx->ngraphs.load() > 0) return nd_set_error(ND_EBUSY, "nd_ctx_destroy: graphs are still loaded");
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    cudaGetLastError();
+    delete ctx;
+    return ND_OK;
+}
+
+extern "C" size_t nd_ctx_bytes_in_use(const nd_ctx* ctx) { return ctx ? ctx->in_use.load() : 0; }
+
+extern "C" int64_t nd_kernel_launches(void) { return nd_total_launches(); }
+
+// ------------------------------------------------------------------------------------
+// graphs
+
+static void free_derived(nd_graph* g) {
+    nd_ctx* c = g->ctx;
+    for (DBuf* b : {&g->split, &g->ebase, &g->pos2e, &g->eu, &g->ev, &g->dg_rp, &g->dg_col, &g->dg_eid, &g->et_rp,
+                    &g->et_w, &g->et_t, &g->tbase, &g->tri_e})
+        nd_free(c, *b);
+    g->have_base = false;
+    g->orient = -1;
+    g->have_tri = false;
+    g->n3 = 0;
+}
+
+extern "C" int nd_load_csr(nd_ctx* ctx, int32_t n, const int64_t* rowptr, const int32_t* col, int flags,
+                           nd_graph** out) {
+    if (!ctx || !out) return nd_set_error(ND_EINVAL, "nd_load_csr: NULL context or out");
+    *out = nullptr;
+    if (n < 0) return nd_set_error(ND_EINVAL, "nd_load_csr: n < 0");
+    if (!rowptr) return nd_set_error(ND_EINVAL, "nd_load_csr: rowptr is NULL");
+    ND_CUDA(cudaSetDevice(ctx->device));
+    bool dev = flags & ND_PTR_DEVICE;
+    int64_t ends[2] = {0, 0};
+    if (dev) {
+        ND_CUDA(cudaMemcpyAsync(ctx->pinned, rowptr, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+        ND_CUDA(cudaMemcpyAsync((char*)ctx->pinned + 8, rowptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                                ctx->stream));
+        ND_TRY(nd_sync(ctx, "nd_load_csr"));
+        memcpy(ends, ctx->pinned, 16);
+    } else {
+        ends[0] = rowptr[0];
+        ends[1] = rowptr[n];
+    }
+    int64_t nnz = ends[1];
+    if (ends[0] != 0 || nnz < 0) return nd_set_error(ND_EINVAL, "nd_load_csr: rowptr[0] must be 0 and rowptr[n] >= 0");
+    if (nnz % 2) return nd_set_error(ND_EINVAL, "nd_load_csr: odd number of entries; the CSR is not symmetric");
+    if (nnz / 2 > INT32_MAX) return nd_set_error(ND_EOVERFLOW, "nd_load_csr: more than 2^31-1 edges");
+    if (nnz > 0 && !col) return nd_set_error(ND_EINVAL, "nd_load_csr: col is NULL");
+    nd_graph* g = new nd_graph();
+    g->ctx = ctx;
+    g->n = n;
+    g->nnz = nnz;
+    g->m = nnz / 2;
+    ctx->ngraphs++;
+    int rc = ND_OK;
+    cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if ((rc = nd_alloc(ctx, g->rp, sizeof(int64_t) * (n + 1))) || (rc = nd_alloc(ctx, g->col, sizeof(int32_t) * nnz)) ||
+        (rc = nd_alloc(ctx, g->scal, 4096))) {
+        nd_graph_free(g);
+        return rc;
+    }
+    if (cudaMemcpyAsync(g->rp.p, rowptr, sizeof(int64_t) * (n + 1), kind, ctx->stream) != cudaSuccess ||
+        (nnz && cudaMemcpyAsync(g->col.p, col, sizeof(int32_t) * nnz, kind, ctx->stream) != cudaSuccess)) {
+        cudaGetLastError();
+        nd_graph_free(g);
+        return nd_set_error(ND_ECUDA, "nd_load_csr: copy failed");
+    }
+    if (flags & ND_VALIDATE) {
+        scalar_zero(g);
+        nd_validate_csr((const int64_t*)g->rp.p, (const int32_t*)g->col.p, n, nnz, (int*)g->scal.p, ctx->stream);
+        int err = 0;
+        if ((rc = nd_check_launch("validate")) || (rc = read_back(g, g->scal.p, &err, "validate"))) {
+            nd_graph_free(g);
+            return rc;
+        }
+        if (err) {
+            nd_graph_free(g);
+            return nd_set_error(ND_EINVAL,
+                                "nd_load_csr: malformed CSR (flags 0x%x: 1 rowptr decreasing, 2 id out of range, "
+                                "4 row not strictly ascending, 8 self-loop, 16 missing reverse entry)",
+                                err);
+        }
+    } else {
+        if ((rc = nd_sync(ctx, "nd_load_csr"))) {
+            nd_graph_free(g);
+            return rc;
+        }
+    }
+    *out = g;
+    return ND_OK;
+}
+
+extern "C" int nd_graph_free(nd_graph* g) {
+    if (!g) return ND_OK;
+    nd_ctx* c = g->ctx;
+    cudaSetDevice(c->device);
+    free_derived(g);
+    for (DBuf* b : {&g->rp, &g->col, &g->scal}) nd_free(c, *b);
+    cudaStreamSynchronize(c->stream);
+    cudaGetLastError();
+    c->ngraphs--;
+    delete g;
+    return ND_OK;
+}
+
+extern "C" int nd_graph_size(const nd_graph* g, int32_t* n, int64_t* m) {
+    if (!g) return nd_set_error(ND_EINVAL, "nd_graph_size: NULL graph");
+    if (n) *n = g->n;
+    if (m) *m = g->m;
+    return ND_OK;
+}
+
+extern "C" int nd_graph_reset(nd_graph* g) {
+    if (!g) return nd_set_error(ND_EINVAL, "nd_graph_reset: NULL graph");
+    cudaSetDevice(g->ctx->device);
+    free_derived(g);
+    return ND_OK;
+}
+
+GraphView nd_view(const nd_graph* g) {
+    GraphView v;
+    memset(&v, 0, sizeof(v));
+    v.n = g->n;
+    v.m = g->m;
+    v.rp = (const int64_t*)g->rp.p;
+    v.col = (const int32_t*)g->col.p;
+    v.split = (const int64_t*)g->split.p;
+    v.ebase = (const int64_t*)g->ebase.p;
+    v.pos2e = (const int32_t*)g->pos2e.p;
+    v.eu = (const int32_t*)g->eu.p;
+    v.ev = (const int32_t*)g->ev.p;
+    v.dg_rp = (const int64_t*)g->dg_rp.p;
+    v.dg_col = (const int32_t*)g->dg_col.p;
+    v.dg_eid = (const int32_t*)g->dg_eid.p;
+    v.et_rp = (const int64_t*)g->et_rp.p;
+    v.et_w = (const int32_t*)g->et_w.p;
+    v.et_t = (const int32_t*)g->et_t.p;
+    v.tbase = (const int64_t*)g->tbase.p;
+    v.tri_e = (const int32_t*)g->tri_e.p;
+    v.n3 = g->n3;
+    return v;
+}
+
+// canonical edge index (r = 2) and the degree bound
+static int ensure_base(nd_graph* g) {
+    if (g->have_base) return ND_OK;
+    nd_ctx* c = g->ctx;
+    cudaStream_t st = c->stream;
+    DBuf updeg, tmp;
+    int rc = ND_OK;
+    if ((rc = nd_alloc(c, g->split, sizeof(int64_t) * std::max<int64_t>(g->n, 1))) ||
+        (rc = nd_alloc(c, g->ebase, sizeof(int64_t) * (g->n + 1))) ||
+        (rc = nd_alloc(c, updeg, sizeof(int64_t) * std::max<int64_t>(g->n, 1))) ||
+        (rc = nd_alloc(c, tmp, nd_scan_tmp_bytes(g->n))) ||
+        (rc = nd_alloc(c, g->pos2e, sizeof(int32_t) * std::max<int64_t>(g->nnz, 1))) ||
+        (rc = nd_alloc(c, g->eu, sizeof(int32_t) * std::max<int64_t>(g->m, 1))) ||
+        (rc = nd_alloc(c, g->ev, sizeof(int32_t) * std::max<int64_t>(g->m, 1)))) {
+        nd_free(c, updeg);
+        nd_free(c, tmp);
+        return rc;
+    }
+    nd_build_split((const int64_t*)g->rp.p, (const int32_t*)g->col.p, g->n, (int64_t*)g->split.p,
+                   (int64_t*)updeg.p, st);
+    nd_scan_i64((const int64_t*)updeg.p, (int64_t*)g->ebase.p, g->n, tmp.p, st);
+    int64_t m_up = 0;
+    rc = nd_check_launch("edge index");
+    if (!rc) rc = read_back(g, (int64_t*)g->ebase.p + g->n, &m_up, "edge index");
+    nd_free(c, updeg);
+    nd_free(c, tmp);
+    if (rc) return rc;
+    if (m_up != g->m)
+        return nd_set_error(ND_EINVAL, "the CSR is not symmetric (%lld upper entries for %lld edges); load it with "
+                                       "ND_VALIDATE for details",
+                            (long long)m_up, (long long)g->m);
+    GraphView v = nd_view(g);
+    ND_TRY(scalar_zero(g));
+    nd_build_pos2e(v, (int32_t*)g->pos2e.p, (int32_t*)g->eu.p, (int32_t*)g->ev.p, (int*)g->scal.p, st);
+    nd_max_deg((const int64_t*)g->rp.p, g->n, (unsigned long long*)g->scal.p + 1, st);
+    unsigned long long sc[2] = {0, 0};
+    ND_TRY(nd_check_launch("edge index"));
+    ND_TRY(read_back(g, g->scal.p, &sc, "edge index"));
+    if (sc[0] & 1)
+        return nd_set_error(ND_EINVAL, "the CSR is not symmetric or has a self-loop; load it with ND_VALIDATE "
+                                       "for details");
+    unsigned long long md = sc[1];
+    g->maxdeg = (int64_t)md;
+    g->have_base = true;
+    return ND_OK;
+}
+
+int nd_kcore_rounds(nd_graph* g, DBuf& rnd_out);  // degeneracy ranking (below)
+
+static int build_dg(nd_graph* g, int mode) {
+    nd_ctx* c = g->ctx;
+    cudaStream_t st = c->stream;
+    DBuf key, outdeg, tmp;
+    int rc = ND_OK;
+    const int32_t* key_hi = nullptr;
+    if (mode == ND_ORIENT_DEGENERACY) {
+        ND_TRY(nd_kcore_rounds(g, key));
+        key_hi = (const int32_t*)key.p;
+    }
+    for (DBuf* b : {&g->dg_rp, &g->dg_col, &g->dg_eid}) nd_free(c, *b);
+    if ((rc = nd_alloc(c, outdeg, sizeof(int64_t) * std::max<int64_t>(g->n, 1))) ||
+        (rc = nd_alloc(c, tmp, nd_scan_tmp_bytes(g->n))) ||
+        (rc = nd_alloc(c, g->dg_rp, sizeof(int64_t) * (g->n + 1))) ||
+        (rc = nd_alloc(c, g->dg_col, sizeof(int32_t) * std::max<int64_t>(g->m, 1))) ||
+        (rc = nd_alloc(c, g->dg_eid, sizeof(int32_t) * std::max<int64_t>(g->m, 1)))) {
+        nd_free(c, key);
+        nd_free(c, outdeg);
+        nd_free(c, tmp);
+        return rc;
+    }
+    GraphView v = nd_view(g);
+    nd_dg_count(v, key_hi, (int64_t*)outdeg.p, st);
+    nd_scan_i64((const int64_t*)outdeg.p, (int64_t*)g->dg_rp.p, g->n, tmp.p, st);
+    v = nd_view(g);
+    nd_dg_fill(v, key_hi, (int64_t*)g->dg_rp.p, (int32_t*)g->dg_col.p, (int32_t*)g->dg_eid.p, st);
+    scalar_zero(g);
+    nd_max_deg((const int64_t*)g->dg_rp.p, g->n, (unsigned long long*)g->scal.p, st);
+    unsigned long long mo = 0;
+    rc = nd_check_launch("orientation");
+    if (!rc) rc = read_back(g, g->scal.p, &mo, "orientation");
+    nd_free(c, key);
+    nd_free(c, outdeg);
+    nd_free(c, tmp);
+    if (rc) return rc;
+    g->maxout = (int64_t)mo;
+    g->orient = mode;
+    return ND_OK;
+}
+
+extern "C" int nd_orient(nd_graph* g, int mode) {
+    if (!g) return nd_set_error(ND_EINVAL, "nd_orient: NULL graph");
+    if (mode != ND_ORIENT_DEGREE && mode != ND_ORIENT_DEGENERACY)
+        return nd_set_error(ND_EINVAL, "nd_orient: unknown mode %d", mode);
+    ND_CUDA(cudaSetDevice(g->ctx->device));
+    ND_TRY(ensure_base(g));
+    if (g->orient == mode) return ND_OK;
+    ND_TRY(build_dg(g, mode));
+    return nd_sync(g->ctx, "nd_orient");
+}
+
+// triangle index (r = 3)
+static int ensure_tri(nd_graph* g) {
+    if (g->have_tri) return ND_OK;
+    nd_ctx* c = g->ctx;
+    cudaStream_t st = c->stream;
+    DBuf sigma, up, tmp;
+    int rc = ND_OK;
+    int64_t m = g->m;
+    if ((rc = nd_alloc(c, sigma, sizeof(int64_t) * std::max<int64_t>(m, 1))) ||
+        (rc = nd_alloc(c, up, sizeof(int64_t) * std::max<int64_t>(m, 1))) ||
+        (rc = nd_alloc(c, tmp, nd_scan_tmp_bytes(m))) || (rc = nd_alloc(c, g->et_rp, sizeof(int64_t) * (m + 1))) ||
+        (rc = nd_alloc(c, g->tbase, sizeof(int64_t) * (m + 1)))) {
+        nd_free(c, sigma);
+        nd_free(c, up);
+        nd_free(c, tmp);
+        return rc;
+    }
+    GraphView v = nd_view(g);
+    nd_edge_support(v, (int64_t*)sigma.p, (int64_t*)up.p, st);
+    nd_scan_i64((const int64_t*)sigma.p, (int64_t*)g->et_rp.p, m, tmp.p, st);
+    nd_scan_i64((const int64_t*)up.p, (int64_t*)g->tbase.p, m, tmp.p, st);
+    int64_t tot[2] = {0, 0};
+    rc = nd_check_launch("triangle index");
+    if (!rc) rc = read_back(g, (int64_t*)g->et_rp.p + m, &tot[0], "triangle index");
+    if (!rc) rc = read_back(g, (int64_t*)g->tbase.p + m, &tot[1], "triangle index");
+    nd_free(c, sigma);
+    nd_free(c, up);
+    nd_free(c, tmp);
+    if (rc) return rc;
+    int64_t n3 = tot[1];
+    if (tot[0] != 3 * n3) return nd_set_error(ND_EINTERNAL, "triangle index: %lld entries for %lld triangles",
+                                              (long long)tot[0], (long long)n3);
+    if (n3 > INT32_MAX) return nd_set_error(ND_EOVERFLOW, "%lld triangles: more than 2^31-1", (long long)n3);
+    if ((rc = nd_alloc(c, g->et_w, sizeof(int32_t) * std::max<int64_t>(3 * n3, 1))) ||
+        (rc = nd_alloc(c, g->et_t, sizeof(int32_t) * std::max<int64_t>(3 * n3, 1))) ||
+        (rc = nd_alloc(c, g->tri_e, sizeof(int32_t) * std::max<int64_t>(3 * n3, 1))))
+        return rc;
+    g->n3 = n3;
+    v = nd_view(g);
+    nd_edge_fill(v, (int64_t*)g->et_rp.p, (int64_t*)g->tbase.p, (int32_t*)g->et_w.p, (int32_t*)g->et_t.p,
+                 (int32_t*)g->tri_e.p, st);
+    v = nd_view(g);
+    nd_edge_fill_tid(v, (int32_t*)g->et_t.p, st);
+    ND_TRY(nd_check_launch("triangle index"));
+    g->have_tri = true;
+    return ND_OK;
+}
+
+static bool rs_supported(int r, int s) {
+    return (r == 1 && (s == 2 || s == 3)) || (r == 2 && (s == 3 || s == 4)) || (r == 3 && s == 4);
+}
+
+static int64_t binom64(int64_t a, int b) {
+    if (b < 0 || a < b) return 0;
+    long double r = 1;
+    for (int i = 1; i <= b; ++i) r = r * (long double)(a - b + i) / i;
+    return r > 9.0e18L ? INT64_MAX : (int64_t)r;
+}
+
+// Prepares orientation and the index for (r,s); *n_r receives the number of r-cliques.
+int nd_prepare(nd_graph* g, int r, int s, int64_t* n_r, double* t_orient, double* t_index) {
+    if (!rs_supported(r, s)) return nd_set_error(ND_EINVAL, "(r,s) = (%d,%d) is not supported", r, s);
+    nd_ctx* c = g->ctx;
+    ND_CUDA(cudaSetDevice(c->device));
+    cudaEvent_t e0, e1, e2;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventCreate(&e2);
+    cudaEventRecord(e0, c->stream);
+    int rc = ensure_base(g);
+    if (!rc && g->orient < 0) rc = build_dg(g, ND_ORIENT_DEGREE);
+    cudaEventRecord(e1, c->stream);
+    if (!rc && r == 3) rc = ensure_tri(g);
+    cudaEventRecord(e2, c->stream);
+    if (!rc) rc = nd_sync(c, "prepare");
+    float a = 0, b = 0;
+    if (!rc) {
+        cudaEventElapsedTime(&a, e0, e1);
+        cudaEventElapsedTime(&b, e1, e2);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaEventDestroy(e2);
+    if (rc) return rc;
+    if (t_orient) *t_orient = a;
+    if (t_index) *t_index = b;
+    *n_r = r == 1 ? g->n : r == 2 ? g->m : g->n3;
+    return ND_OK;
+}
+
+// An upper bound on any count: the s-cliques containing R are R plus an (s-r)-clique among
+// the common neighbours of R, at most C(maxdeg, s-r) of them.
+static int64_t count_bound(const nd_graph* g, int r, int s) { return binom64(g->maxdeg, s - r); }
+
+// Runs the counting kernels into a fresh buffer of width w (4 or 8); *cnt receives it.
+int nd_count_into(nd_graph* g, int r, int s, int w, int64_t n_r, DBuf& cnt) {
+    nd_ctx* c = g->ctx;
+    cudaStream_t st = c->stream;
+    GraphView v = nd_view(g);
+    ND_TRY(nd_alloc(c, cnt, (size_t)w * std::max<int64_t>(n_r, 1)));
+    if (w == 8) {
+        nd_count_launch<int64_t>(v, r, s, (int64_t*)cnt.p, n_r, st);
+        return nd_check_launch("count");
+    }
+    if (count_bound(g, r, s) <= INT32_MAX) {
+        nd_count_launch<int32_t>(v, r, s, (int32_t*)cnt.p, n_r, st);
+        return nd_check_launch("count");
+    }
+    // width 4 requested but counts may not fit: count in int64, then narrow with a check
+    DBuf wide;
+    ND_TRY(nd_alloc(c, wide, 8 * std::max<int64_t>(n_r, 1)));
+    nd_count_launch<int64_t>(v, r, s, (int64_t*)wide.p, n_r, st);
+    scalar_zero(g);
+    nd_narrow_i64((const int64_t*)wide.p, (int32_t*)cnt.p, n_r, (int*)g->scal.p, st);
+    int err = 0;
+    int rc = nd_check_launch("count");
+    if (!rc) rc = read_back(g, g->scal.p, &err, "count");
+    nd_free(c, wide);
+    if (rc) return rc;
+    if (err) return nd_set_error(ND_EOVERFLOW, "an s-clique count exceeds 2^31-1; use count_width 8");
+    return ND_OK;
+}
+
+int nd_pick_width(const nd_graph* g, int r, int s, int count_width, int* w) {
+    if (count_width != 0 && count_width != 4 && count_width != 8)
+        return nd_set_error(ND_EINVAL, "count_width must be 0, 4 or 8");
+    *w = count_width ? count_width : (count_bound(g, r, s) <= INT32_MAX ? 4 : 8);
+    return ND_OK;
+}
+
+static int sum_counts(nd_graph* g, const DBuf& cnt, int w, int64_t n_r, unsigned long long* out) {
+    ND_TRY(scalar_zero(g));
+    if (w == 8)
+        nd_sum_i64((const int64_t*)cnt.p, n_r, (unsigned long long*)g->scal.p, g->ctx->stream);
+    else
+        nd_sum_i32((const int32_t*)cnt.p, n_r, (unsigned long long*)g->scal.p, g->ctx->stream);
+    ND_TRY(nd_check_launch("sum"));
+    return read_back(g, g->scal.p, out, "sum");
+}
+
+extern "C" int nd_count(nd_graph* g, int r, int s, int count_width, void* counts_out, int flags, int64_t* n_r_out,
+                        int64_t* n_s_out) {
+    if (!g) return nd_set_error(ND_EINVAL, "nd_count: NULL graph");
+    int64_t n_r = 0;
+    ND_TRY(nd_prepare(g, r, s, &n_r, nullptr, nullptr));
+    if (n_r_out) *n_r_out = n_r;
+    int w = 0;
+    ND_TRY(nd_pick_width(g, r, s, count_width, &w));
+    if (!counts_out && !n_s_out) return ND_OK;
+    DBuf cnt;
+    int rc = nd_count_into(g, r, s, w, n_r, cnt);
+    unsigned long long tot = 0;
+    if (!rc && n_s_out) rc = sum_counts(g, cnt, w, n_r, &tot);
+    if (!rc && counts_out && n_r > 0) {
+        cudaError_t e = cudaMemcpyAsync(counts_out, cnt.p, (size_t)w * n_r,
+                                        (flags & ND_PTR_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                        g->ctx->stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            rc = nd_set_error(ND_ECUDA, "nd_count: copy out: %s", cudaGetErrorString(e));
+        }
+    }
+    if (!rc) rc = nd_sync(g->ctx, "nd_count");
+    nd_free(g->ctx, cnt);
+    if (!rc && n_s_out) *n_s_out = (int64_t)(tot / (unsigned long long)binom64(s, r));
+    return rc;
+}
+
+// ------------------------------------------------------------------------------------
+// peeling
+
+template <typename CT>
+static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags, PeelOut& po) {
+    nd_ctx* c = g->ctx;
+    cudaStream_t st = c->stream;
+    int64_t cap = std::max<int64_t>(n_r, 1);
+    int64_t rcap = std::min<int64_t>(n_r, (int64_t)1 << 22) + 1;
+    DBuf ctl, A0, A1, N0, N1, L0, L1, rs, rl;
+    int rc = ND_OK;
+    if ((rc = nd_alloc(c, ctl, sizeof(PeelCtl))) || (rc = nd_alloc(c, A0, 4 * cap)) || (rc = nd_alloc(c, A1, 4 * cap)) ||
+        (rc = nd_alloc(c, N0, 4 * cap)) || (rc = nd_alloc(c, N1, 4 * cap)) || (rc = nd_alloc(c, L0, 4 * cap)) ||
+        (rc = nd_alloc(c, L1, 4 * cap)) || (rc = nd_alloc(c, rs, 8 * rcap)) || (rc = nd_alloc(c, rl, 8 * rcap))) {
+        for (DBuf* b : {&ctl, &A0, &A1, &N0, &N1, &L0, &L1, &rs, &rl}) nd_free(c, *b);
+        return rc;
+    }
+    PeelView<CT> P;
+    P.cnt = (CT*)cnt.p;
+    P.rnd = (int32_t*)po.rnd.p;
+    P.core = (int32_t*)po.core.p;
+    P.A[0] = (int32_t*)A0.p;
+    P.A[1] = (int32_t*)A1.p;
+    P.N[0] = (int32_t*)N0.p;
+    P.N[1] = (int32_t*)N1.p;
+    P.L[0] = (int32_t*)L0.p;
+    P.L[1] = (int32_t*)L1.p;
+    P.cap = (uint32_t)cap;
+    P.ctl = (PeelCtl*)ctl.p;
+    P.round_size = (int64_t*)rs.p;
+    P.round_level = (int64_t*)rl.p;
+    P.round_cap = rcap;
+    nd_fill_i32(P.rnd, ND_UNPEELED, n_r, st);
+    nd_fill_i32(P.core, 0, n_r, st);
+    nd_peel_init(P.ctl, n_r, n_r + 2, st);
+    GraphView v = nd_view(g);
+    const int kChunk = 32;
+    int64_t max_chunks = (n_r + 2) / kChunk + 4;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    size_t graph_nodes = 0;
+    bool use_graph = !(flags & ND_NO_GRAPH);
+    if (use_graph) {
+        cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            nd_set_capturing(true);
+            for (int i = 0; i < kChunk; ++i) nd_peel_round<CT>(v, r, s, P, st);
+            nd_set_capturing(false);
+            e = cudaStreamEndCapture(st, &graph);
+        }
+        if (e == cudaSuccess) e = cudaGraphGetNodes(graph, nullptr, &graph_nodes);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            if (graph) cudaGraphDestroy(graph);
+            graph = nullptr;
+            exec = nullptr;
+            use_graph = false;
+        }
+    }
+    int32_t* hdone = (int32_t*)c->pinned;
+    rc = ND_OK;
+    int64_t chunks = 0;
+    for (;;) {
+        if (use_graph) {
+            cudaGraphLaunch(exec, st);
+            nd_note_launches((int64_t)graph_nodes);
+        } else {
+            for (int i = 0; i < kChunk; ++i) nd_peel_round<CT>(v, r, s, P, st);
+        }
+        if ((rc = nd_check_launch("peel round"))) break;
+        cudaMemcpyAsync(hdone, &P.ctl->done, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+        if ((rc = nd_sync(c, "peel round"))) break;
+        if (*hdone) break;
+        if (++chunks > max_chunks) {
+            rc = nd_set_error(ND_ETIMEOUT, "peeling did not finish within %lld rounds", (long long)(chunks * kChunk));
+            break;
+        }
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (!rc) {
+        PeelCtl h;
+        cudaMemcpyAsync(c->pinned, P.ctl, std::min<size_t>(sizeof(PeelCtl), 4096), cudaMemcpyDeviceToHost, st);
+        rc = nd_sync(c, "peel stats");
+        if (!rc) {
+            memcpy(&h, c->pinned, std::min<size_t>(sizeof(PeelCtl), 4096));
+            if (h.err & 1) rc = nd_set_error(ND_EINTERNAL, "peel: a work list overflowed");
+            else if (h.err & 2) rc = nd_set_error(ND_ETIMEOUT, "peel: round cap reached");
+            else if (h.err & 4) rc = nd_set_error(ND_EINTERNAL, "peel: empty round (inconsistent state)");
+            else if (h.finished != n_r) rc = nd_set_error(ND_EINTERNAL, "peel: finished %lld of %lld",
+                                                          (long long)h.finished, (long long)n_r);
+            po.rho = h.t;
+            po.max_core = n_r ? h.k : 0;
+            po.listed = (int64_t)h.listed;
+            po.advances = h.advances;
+            po.refills = h.refills;
+            if (h.k > INT32_MAX && !rc) rc = nd_set_error(ND_EOVERFLOW, "a core number exceeds 2^31-1");
+        }
+    }
+    if (!rc) {
+        int64_t nrec = std::min<int64_t>(po.rho, rcap);
+        po.sizes.resize(nrec);
+        po.levels.resize(nrec);
+        if (nrec) {
+            cudaMemcpyAsync(po.sizes.data(), rs.p, 8 * nrec, cudaMemcpyDeviceToHost, st);
+            cudaMemcpyAsync(po.levels.data(), rl.p, 8 * nrec, cudaMemcpyDeviceToHost, st);
+            rc = nd_sync(c, "peel record");
+        }
+    }
+    for (DBuf* b : {&ctl, &A0, &A1, &N0, &N1, &L0, &L1, &rs, &rl}) nd_free(c, *b);
+    return rc;
+}
+
+int nd_decompose_dev(nd_graph* g, int r, int s, int count_width, int flags, PeelOut& po, nd_stats* st) {
+    nd_ctx* c = g->ctx;
+    nd_stats S;
+    memset(&S, 0, sizeof(S));
+    int64_t n_r = 0;
+    double t_or = 0, t_ix = 0;
+    ND_TRY(nd_prepare(g, r, s, &n_r, &t_or, &t_ix));
+    int w = 0;
+    ND_TRY(nd_pick_width(g, r, s, count_width, &w));
+    cudaEvent_t e0, e1, e2, e3;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventCreate(&e2);
+    cudaEventCreate(&e3);
+    DBuf cnt;
+    int rc = nd_alloc(c, po.core, 4 * std::max<int64_t>(n_r, 1));
+    if (!rc) rc = nd_alloc(c, po.rnd, 4 * std::max<int64_t>(n_r, 1));
+    cudaEventRecord(e0, c->stream);
+    if (!rc) rc = nd_count_into(g, r, s, w, n_r, cnt);
+    cudaEventRecord(e1, c->stream);
+    unsigned long long tot = 0;
+    if (!rc) rc = sum_counts(g, cnt, w, n_r, &tot);
+    cudaEventRecord(e3, c->stream);
+    if (!rc) rc = (w == 8) ? run_peel<int64_t>(g, r, s, cnt, n_r, flags, po) : run_peel<int32_t>(g, r, s, cnt, n_r, flags, po);
+    cudaEventRecord(e2, c->stream);
+    if (!rc) rc = nd_sync(c, "nd_decompose");
+    float tc = 0, tp = 0;
+    if (!rc) {
+        cudaEventElapsedTime(&tc, e0, e1);
+        cudaEventElapsedTime(&tp, e3, e2);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaEventDestroy(e2);
+    cudaEventDestroy(e3);
+    nd_free(c, cnt);
+    if (rc) return rc;
+    S.n_r = n_r;
+    S.n_s = (int64_t)(tot / (unsigned long long)binom64(s, r));
+    S.rho = po.rho;
+    S.max_core = po.max_core;
+    S.listed = po.listed;
+    S.advances = po.advances;
+    S.refills = po.refills;
+    S.count_width = w;
+    S.orient_mode = g->orient;
+    S.t_orient_ms = t_or;
+    S.t_index_ms = t_ix;
+    S.t_count_ms = tc;
+    S.t_peel_ms = tp;
+    S.t_total_ms = t_or + t_ix + tc + tp;
+    if (st) *st = S;
+    return ND_OK;
+}
+
+extern "C" int nd_decompose(nd_graph* g, int r, int s, int count_width, int32_t* core_out, int32_t* round_out,
+                            int flags, nd_stats* st) {
+    if (!g) return nd_set_error(ND_EINVAL, "nd_decompose: NULL graph");
+    PeelOut po;
+    int rc = nd_decompose_dev(g, r, s, count_width, flags, po, st);
+    nd_ctx* c = g->ctx;
+    if (!rc) {
+        int64_t n_r = (r == 1) ? g->n : (r == 2) ? g->m : g->n3;
+        cudaMemcpyKind kind = (flags & ND_PTR_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        cudaError_t e = cudaSuccess;
+        if (core_out && n_r) e = cudaMemcpyAsync(core_out, po.core.p, 4 * n_r, kind, c->stream);
+        if (e == cudaSuccess && round_out && n_r) e = cudaMemcpyAsync(round_out, po.rnd.p, 4 * n_r, kind, c->stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            rc = nd_set_error(ND_ECUDA, "nd_decompose: copy out: %s", cudaGetErrorString(e));
+        }
+        if (!rc) rc = nd_sync(c, "nd_decompose");
+        g->last_sizes = po.sizes;
+        g->last_levels = po.levels;
+        g->last_rho = po.rho;
+        g->have_last = true;
+    }
+    nd_free(c, po.core);
+    nd_free(c, po.rnd);
+    return rc;
+}
+
+extern "C" int nd_rounds(nd_graph* g, int64_t* sizes_out, int64_t* levels_out, int64_t cap, int64_t* rho_out) {
+    if (!g) return nd_set_error(ND_EINVAL, "nd_rounds: NULL graph");
+    if (!g->have_last) return nd_set_error(ND_EINVAL, "nd_rounds: no decomposition has run on this graph");
+    int64_t k = std::min<int64_t>(cap, (int64_t)g->last_sizes.size());
+    for (int64_t i = 0; i < k; ++i) {
+        if (sizes_out) sizes_out[i] = g->last_sizes[i];
+        if (levels_out) levels_out[i] = g->last_levels[i];
+    }
+    if (rho_out) *rho_out = g->last_rho;
+    return ND_OK;
+}
+
+extern "C" int nd_rcliques(nd_graph* g, int r, int32_t* tuples_out, int flags, int64_t* n_r_out) {
+    if (!g) return nd_set_error(ND_EINVAL, "nd_rcliques: NULL graph");
+    if (r < 1 || r > 3) return nd_set_error(ND_EINVAL, "nd_rcliques: r must be 1, 2 or 3");
+    int64_t n_r = 0;
+    ND_TRY(nd_prepare(g, r, r + 1, &n_r, nullptr, nullptr));
+    if (n_r_out) *n_r_out = n_r;
+    if (!tuples_out || n_r == 0) return ND_OK;
+    nd_ctx* c = g->ctx;
+    DBuf out;
+    ND_TRY(nd_alloc(c, out, sizeof(int32_t) * r * n_r));
+    GraphView v = nd_view(g);
+    if (r == 1)
+        nd_iota_i32((int32_t*)out.p, n_r, c->stream);
+    else if (r == 2)
+        nd_edge_tuples(v, (int32_t*)out.p, c->stream);
+    else
+        nd_tri_tuples(v, (int32_t*)out.p, c->stream);
+    int rc = nd_check_launch("rcliques");
+    if (!rc) {
+        cudaError_t e = cudaMemcpyAsync(tuples_out, out.p, sizeof(int32_t) * r * n_r,
+                                        (flags & ND_PTR_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                        c->stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            rc = nd_set_error(ND_ECUDA, "nd_rcliques: %s", cudaGetErrorString(e));
+        }
+    }
+    if (!rc) rc = nd_sync(c, "nd_rcliques");
+    nd_free(c, out);
+    return rc;
+}
+
+// Degeneracy ranking for ND_ORIENT_DEGENERACY: the round in which each vertex leaves the
+// k-core peeling ((1,2) decomposition); ties inside a round are broken by vertex id.
+int nd_kcore_rounds(nd_graph* g, DBuf& rnd_out) {
+    nd_ctx* c = g->ctx;
+    int64_t n = g->n;
+    DBuf cnt;
+    PeelOut po;
+    int rc = nd_alloc(c, po.core, 4 * std::max<int64_t>(n, 1));
+    if (!rc) rc = nd_alloc(c, po.rnd, 4 * std::max<int64_t>(n, 1));
+    if (!rc) rc = nd_count_into(g, 1, 2, 4, n, cnt);
+    if (!rc) rc = run_peel<int32_t>(g, 1, 2, cnt, n, 0, po);
+    nd_free(c, cnt);
+    nd_free(c, po.core);
+    if (rc) {
+        nd_free(c, po.rnd);
+        return rc;
+    }
+    rnd_out = po.rnd;
+    po.rnd.p = nullptr;
+    po.rnd.bytes = 0;
+    return ND_OK;
+}

@@ -1,0 +1,209 @@
+// Internal declarations shared by the CUDA translation units of libnd.so.
+//
+// Data layout in HBM (all arrays are plain device buffers owned by an nd_graph):
+//   undirected CSR       rp int64[n+1], col int32[2m]          (caller's ids, rows ascending)
+//   canonical edge index split int64[n]   first row position with col > row
+//                        ebase int64[n+1]  exclusive scan of upper degrees
+//                        pos2e int32[2m]   canonical edge id of every CSR entry
+//                        eu, ev int32[m]   endpoints (eu < ev) of every canonical edge
+//   oriented graph DG    dg_rp int64[n+1], dg_col int32[m], dg_eid int32[m]
+//                        (out-lists keep the ascending-id order of the CSR rows)
+//   triangle index       et_rp int64[m+1]  per canonical edge (a,b): start of L(a,b)
+//     (r = 3)            et_w int32[3 n3]  L(a,b) = N(a) ∩ N(b), ascending
+//                        et_t int32[3 n3]  canonical id of triangle {a,b,w} per entry
+//                        tbase int64[m+1]  exclusive scan of |{w in L(a,b) : w > b}|
+//                        tri_e int32[3 n3] edges (ab, ac, bc) of triangle (a<b<c)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define ND_UNPEELED 0x7fffffff
+#define ND_WARP 32
+
+// ------------------------------------------------------------------------------------
+// device helpers
+
+// first index i in [0, n) with a[i] >= x (n if none)
+__device__ __forceinline__ int64_t nd_lower_bound(const int32_t* __restrict__ a, int64_t n, int32_t x) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (__ldg(a + mid) < x)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// index of x in the ascending list a[0, n), or -1
+__device__ __forceinline__ int64_t nd_find(const int32_t* __restrict__ a, int64_t n, int32_t x) {
+    int64_t i = nd_lower_bound(a, n, x);
+    return (i < n && __ldg(a + i) == x) ? i : -1;
+}
+
+__device__ __forceinline__ unsigned nd_lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Warp-aggregated append: every active lane gets its own slot in list[] (capacity cap);
+// one atomicAdd per converged group of lanes. Returns the slot, or -1 if the list is full.
+__device__ __forceinline__ int64_t nd_append(unsigned int* counter, int32_t* list, uint32_t cap, int32_t value,
+                                             int* err) {
+    unsigned mask = __activemask();
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(mask) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(counter, (unsigned)__popc(mask));
+    base = __shfl_sync(mask, base, leader);
+    unsigned slot = base + __popc(mask & nd_lanemask_lt());
+    if (slot >= cap) {
+        atomicExch(err, 1);
+        return -1;
+    }
+    list[slot] = value;
+    return slot;
+}
+
+__device__ __forceinline__ int64_t nd_atomic_dec(int32_t* p) { return (int64_t)atomicSub(p, 1); }
+__device__ __forceinline__ int64_t nd_atomic_dec(int64_t* p) {
+    return (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(p), 0xffffffffffffffffull);
+}
+__device__ __forceinline__ void nd_atomic_add(int32_t* p, int64_t v) { atomicAdd(p, (int)v); }
+__device__ __forceinline__ void nd_atomic_add(int64_t* p, int64_t v) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
+}
+
+// ------------------------------------------------------------------------------------
+// device views
+
+struct GraphView {
+    int32_t n;
+    int64_t m;  // undirected edges
+    const int64_t* rp;
+    const int32_t* col;
+    const int64_t* split;
+    const int64_t* ebase;
+    const int32_t* pos2e;
+    const int32_t* eu;
+    const int32_t* ev;
+    const int64_t* dg_rp;
+    const int32_t* dg_col;
+    const int32_t* dg_eid;
+    const int64_t* et_rp;
+    const int32_t* et_w;
+    const int32_t* et_t;
+    const int64_t* tbase;
+    const int32_t* tri_e;
+    int64_t n3;
+};
+
+// Control block of the device-resident peeling loop (one per decomposition).
+// A round t runs: ctl -> adv_min -> refill (4 kernels) -> adv_select -> update. Only ctl is
+// a one-thread kernel; the others early-exit when their phase is not needed this round.
+#define ND_HBINS 4096
+#define ND_MODE_ADV 1
+
+struct PeelCtl {
+    // loop state
+    int32_t t;          // current round
+    int32_t mode;       // ND_MODE_ADV when this round moves to a new level
+    int32_t done;       // 1 once every r-clique is peeled
+    int32_t err;        // list overflow / inconsistency
+    int32_t started;    // 0 before the first round
+    int32_t wa, wn, wl; // ping-pong selectors of the A, N and L lists
+    int32_t lmat;       // 0: L is implicitly 0..n_r-1
+    int32_t pad0;
+    int64_t k;          // current level
+    int64_t hi;         // bucket window: N holds every unpeeled r-clique with count < hi
+    int64_t finished;   // r-cliques peeled so far
+    int64_t n_r;
+    int64_t max_rounds; // round cap (ND_ETIMEOUT)
+    // list sizes
+    unsigned int nA;    // |A| of a same-level round
+    unsigned int cntA;  // |A| written by adv_select
+    unsigned int nNext; // next round's A (r-cliques that fell to <= k during this round)
+    unsigned int nN;    // |N| (current)
+    unsigned int nN2;   // |N'| being written this round (advance rounds)
+    unsigned int nL;    // |L|
+    unsigned int nL2;   // |L'| being written by refill
+    unsigned int pad1;
+    unsigned long long minN;  // min count over unpeeled members of N (adv_min)
+    unsigned long long gmin;  // min count over unpeeled r-cliques (refill)
+    // statistics
+    unsigned long long listed;
+    long long advances, refills;
+    unsigned long long hist[ND_HBINS];
+};
+
+template <typename CT>
+struct PeelView {
+    CT* cnt;
+    int32_t* rnd;
+    int32_t* core;
+    int32_t* A[2];
+    int32_t* N[2];
+    int32_t* L[2];
+    uint32_t cap;
+    PeelCtl* ctl;
+    int64_t* round_size;
+    int64_t* round_level;
+    int64_t round_cap;
+};
+
+// ------------------------------------------------------------------------------------
+// launch accounting: every kernel launch goes through ND_K, which adds one to a process-wide
+// counter (launches recorded while a stream is being captured into a CUDA graph are not
+// counted; graph replays add their node count instead)
+void nd_note_launches(int64_t k);
+int64_t nd_total_launches();
+void nd_set_capturing(bool on);
+#define ND_K(...) (nd_note_launches(1), __VA_ARGS__)
+
+// ------------------------------------------------------------------------------------
+// host launchers (all enqueue on `st`, none synchronises)
+
+// out[0..n] = exclusive scan of in[0..n), out[n] = total. tmp: nd_scan_tmp_bytes(n) bytes.
+size_t nd_scan_tmp_bytes(int64_t n);
+void nd_scan_i64(const int64_t* in, int64_t* out, int64_t n, void* tmp, cudaStream_t st);
+void nd_fill_i32(int32_t* p, int32_t v, int64_t n, cudaStream_t st);
+void nd_iota_i32(int32_t* p, int64_t n, cudaStream_t st);
+// *out = max over a[0..n) (int64 device scalar, must be pre-set to 0)
+void nd_max_i64(const int64_t* a, int64_t n, unsigned long long* out, cudaStream_t st);
+void nd_max_deg(const int64_t* rp, int32_t n, unsigned long long* out, cudaStream_t st);
+void nd_sum_i64(const int64_t* a, int64_t n, unsigned long long* out, cudaStream_t st);
+void nd_sum_i32(const int32_t* a, int64_t n, unsigned long long* out, cudaStream_t st);
+void nd_max_i32(const int32_t* a, int64_t n, unsigned long long* out, cudaStream_t st);
+// narrow int64 counts to int32; *err set to 1 if a value exceeds INT32_MAX
+void nd_narrow_i64(const int64_t* in, int32_t* out, int64_t n, int* err, cudaStream_t st);
+
+// graph structure (nd_graph.cu)
+void nd_validate_csr(const int64_t* rp, const int32_t* col, int32_t n, int64_t nnz, int* err, cudaStream_t st);
+void nd_build_split(const int64_t* rp, const int32_t* col, int32_t n, int64_t* split, int64_t* updeg,
+                    cudaStream_t st);
+void nd_build_pos2e(const GraphView& g, int32_t* pos2e, int32_t* eu, int32_t* ev, int* err, cudaStream_t st);
+// key(v) = (key_hi[v] or degree, v); key_hi NULL means degree
+void nd_dg_count(const GraphView& g, const int32_t* key_hi, int64_t* outdeg, cudaStream_t st);
+void nd_dg_fill(const GraphView& g, const int32_t* key_hi, int64_t* dg_rp_in, int32_t* dg_col, int32_t* dg_eid,
+                cudaStream_t st);
+// per canonical edge: sigma = |N(a) ∩ N(b)|, up = |{w in N(a) ∩ N(b) : w > b}|
+void nd_edge_support(const GraphView& g, int64_t* sigma, int64_t* up, cudaStream_t st);
+void nd_edge_fill(const GraphView& g, int64_t* et_rp, int64_t* tbase, int32_t* et_w, int32_t* et_t,
+                  int32_t* tri_e, cudaStream_t st);
+void nd_edge_fill_tid(const GraphView& g, int32_t* et_t, cudaStream_t st);
+void nd_tri_tuples(const GraphView& g, int32_t* out, cudaStream_t st);
+void nd_edge_tuples(const GraphView& g, int32_t* out, cudaStream_t st);
+
+// counting (nd_count.cu): counts into cnt (CT = int32_t or int64_t), zero-initialised
+template <typename CT>
+void nd_count_launch(const GraphView& g, int r, int s, CT* cnt, int64_t n_r, cudaStream_t st);
+
+// peeling (nd_peel.cu)
+template <typename CT>
+void nd_peel_round(const GraphView& g, int r, int s, const PeelView<CT>& P, cudaStream_t st);
+void nd_peel_init(PeelCtl* ctl, int64_t n_r, int64_t max_rounds, cudaStream_t st);
+
+int nd_sm_count();

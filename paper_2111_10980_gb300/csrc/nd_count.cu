@@ -1,0 +1,189 @@
+// s-clique counts per r-clique: Algorithm 2's Count-Func over every s-clique listed once by
+// Algorithm 1 (rec-list-cliques) on the oriented graph DG.
+//
+// Two kernel shapes, one per kind of (r,s):
+//   * s = r + 1  ((1,2), (2,3), (3,4)): the s-cliques containing R are R plus one vertex of
+//     I(R) = ∩_{v in R} N(v), so count[R] = |I(R)|. One warp per r-clique walks the shortest
+//     list and binary-searches the others; the result is written once, with no atomics.
+//     For r = 3 the lists are the per-edge common-neighbour tables L(e) of the triangle index
+//     (|L(e)| is the edge's triangle support, far shorter than the vertex degrees).
+//   * s = r + 2  ((1,3), (2,4)): one warp per vertex u lists the s-cliques whose lowest vertex
+//     in the orientation is u (Algorithm 1 over DG: I' = I ∩ N_DG(v) at each level) and adds 1
+//     to each of their C(s,r) r-subsets (Count-Func), with one aggregated atomic for the
+//     r-subsets shared by a whole level.
+#include "nd_common.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarpsPerBlock = kThreads / 32;
+
+int blocks_for_warps(int64_t items) {
+    int64_t want = (items + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    int64_t cap = (int64_t)nd_sm_count() * 16;
+    if (want < 1) want = 1;
+    return (int)(want < cap ? want : cap);
+}
+
+__device__ __forceinline__ int64_t gwarp() { return ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; }
+__device__ __forceinline__ int64_t nwarps() { return ((int64_t)gridDim.x * blockDim.x) >> 5; }
+
+__device__ __forceinline__ int warp_sum(int v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename CT>
+__global__ void k_count12(GraphView g, CT* __restrict__ cnt) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < g.n; v += (int64_t)gridDim.x * blockDim.x)
+        cnt[v] = (CT)(g.rp[v + 1] - g.rp[v]);
+}
+
+// count[e] = |N(a) ∩ N(b)|
+template <typename CT>
+__global__ void k_count23(GraphView g, CT* __restrict__ cnt) {
+    int lane = threadIdx.x & 31;
+    for (int64_t e = gwarp(); e < g.m; e += nwarps()) {
+        int32_t a = g.eu[e], b = g.ev[e];
+        int64_t ab = g.rp[a], ae = g.rp[a + 1], bb = g.rp[b], be = g.rp[b + 1];
+        const int32_t *xs = g.col + ab, *ys = g.col + bb;
+        int64_t nx = ae - ab, ny = be - bb;
+        if (nx > ny) {
+            const int32_t* t = xs;
+            xs = ys;
+            ys = t;
+            int64_t tn = nx;
+            nx = ny;
+            ny = tn;
+        }
+        int c = 0;
+        for (int64_t i = lane; i < nx; i += 32) c += nd_find(ys, ny, xs[i]) >= 0 ? 1 : 0;
+        c = warp_sum(c);
+        if (lane == 0) cnt[e] = (CT)c;
+    }
+}
+
+// count[t] = |L(ab) ∩ L(ac) ∩ L(bc)|
+template <typename CT>
+__global__ void k_count34(GraphView g, CT* __restrict__ cnt) {
+    int lane = threadIdx.x & 31;
+    for (int64_t t = gwarp(); t < g.n3; t += nwarps()) {
+        int32_t e0 = g.tri_e[3 * t], e1 = g.tri_e[3 * t + 1], e2 = g.tri_e[3 * t + 2];
+        int64_t b0 = g.et_rp[e0], n0 = g.et_rp[e0 + 1] - b0;
+        int64_t b1 = g.et_rp[e1], n1 = g.et_rp[e1 + 1] - b1;
+        int64_t b2 = g.et_rp[e2], n2 = g.et_rp[e2 + 1] - b2;
+        // drive with the shortest list
+        if (n1 < n0) {
+            int64_t tb = b0, tn = n0;
+            b0 = b1, n0 = n1, b1 = tb, n1 = tn;
+        }
+        if (n2 < n0) {
+            int64_t tb = b0, tn = n0;
+            b0 = b2, n0 = n2, b2 = tb, n2 = tn;
+        }
+        int c = 0;
+        for (int64_t i = lane; i < n0; i += 32) {
+            int32_t w = g.et_w[b0 + i];
+            if (nd_find(g.et_w + b1, n1, w) >= 0 && nd_find(g.et_w + b2, n2, w) >= 0) c++;
+        }
+        c = warp_sum(c);
+        if (lane == 0) cnt[t] = (CT)c;
+    }
+}
+
+// (1,3): every triangle (u, v, w) of DG (u -> v, u -> w, v -> w) adds 1 to u, v and w.
+template <typename CT>
+__global__ void k_count13(GraphView g, CT* __restrict__ cnt) {
+    int lane = threadIdx.x & 31;
+    for (int64_t u = gwarp(); u < g.n; u += nwarps()) {
+        int64_t ub = g.dg_rp[u], ue = g.dg_rp[u + 1];
+        int cu = 0;
+        for (int64_t jv = ub; jv < ue; ++jv) {
+            int32_t v = g.dg_col[jv];
+            int64_t vb = g.dg_rp[v], vn = g.dg_rp[v + 1] - vb;
+            int cv = 0;
+            for (int64_t i = ub + lane; i < ue; i += 32) {
+                int32_t w = g.dg_col[i];
+                if (nd_find(g.dg_col + vb, vn, w) >= 0) {
+                    nd_atomic_add(&cnt[w], 1);
+                    cv++;
+                }
+            }
+            cv = warp_sum(cv);
+            if (lane == 0 && cv) nd_atomic_add(&cnt[v], cv);
+            cu += cv;
+        }
+        if (lane == 0 && cu) nd_atomic_add(&cnt[u], cu);
+    }
+}
+
+// (2,4): every 4-clique (u, v, w, x) of DG adds 1 to its six edges.
+template <typename CT>
+__global__ void k_count24(GraphView g, CT* __restrict__ cnt) {
+    int lane = threadIdx.x & 31;
+    for (int64_t u = gwarp(); u < g.n; u += nwarps()) {
+        int64_t ub = g.dg_rp[u], ue = g.dg_rp[u + 1];
+        for (int64_t jv = ub; jv < ue; ++jv) {
+            int32_t v = g.dg_col[jv];
+            int32_t e_uv = g.dg_eid[jv];
+            int64_t vb = g.dg_rp[v], vn = g.dg_rp[v + 1] - vb;
+            int c_uv = 0;
+            for (int64_t i = ub + lane; i < ue; i += 32) {
+                int32_t w = g.dg_col[i];
+                int64_t q = nd_find(g.dg_col + vb, vn, w);
+                if (q < 0) continue;
+                int32_t e_uw = g.dg_eid[i], e_vw = g.dg_eid[vb + q];
+                int64_t wb = g.dg_rp[w], we = g.dg_rp[w + 1];
+                int c_w = 0;
+                for (int64_t jx = wb; jx < we; ++jx) {
+                    int32_t x = g.dg_col[jx];
+                    int64_t pux = nd_find(g.dg_col + ub, ue - ub, x);
+                    if (pux < 0) continue;
+                    int64_t pvx = nd_find(g.dg_col + vb, vn, x);
+                    if (pvx < 0) continue;
+                    c_w++;
+                    nd_atomic_add(&cnt[g.dg_eid[ub + pux]], 1);
+                    nd_atomic_add(&cnt[g.dg_eid[vb + pvx]], 1);
+                    nd_atomic_add(&cnt[g.dg_eid[jx]], 1);
+                }
+                if (c_w) {
+                    nd_atomic_add(&cnt[e_uw], c_w);
+                    nd_atomic_add(&cnt[e_vw], c_w);
+                    c_uv += c_w;
+                }
+            }
+            c_uv = warp_sum(c_uv);
+            if (lane == 0 && c_uv) nd_atomic_add(&cnt[e_uv], c_uv);
+        }
+    }
+}
+
+template <typename CT>
+__global__ void k_zero(CT* p, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = 0;
+}
+
+}  // namespace
+
+template <typename CT>
+void nd_count_launch(const GraphView& g, int r, int s, CT* cnt, int64_t n_r, cudaStream_t st) {
+    if (n_r <= 0) return;
+    int blk = blocks_for_warps(n_r);
+    if (r == 1 && s == 2) {
+        ND_K(k_count12<CT><<<blk, kThreads, 0, st>>>(g, cnt));
+    } else if (r == 2 && s == 3) {
+        ND_K(k_count23<CT><<<blk, kThreads, 0, st>>>(g, cnt));
+    } else if (r == 3 && s == 4) {
+        ND_K(k_count34<CT><<<blk, kThreads, 0, st>>>(g, cnt));
+    } else if (r == 1 && s == 3) {
+        ND_K(k_zero<CT><<<blk, kThreads, 0, st>>>(cnt, n_r));
+        ND_K(k_count13<CT><<<blocks_for_warps(g.n), kThreads, 0, st>>>(g, cnt));
+    } else if (r == 2 && s == 4) {
+        ND_K(k_zero<CT><<<blk, kThreads, 0, st>>>(cnt, n_r));
+        ND_K(k_count24<CT><<<blocks_for_warps(g.n), kThreads, 0, st>>>(g, cnt));
+    }
+}
+
+template void nd_count_launch<int32_t>(const GraphView&, int, int, int32_t*, int64_t, cudaStream_t);
+template void nd_count_launch<int64_t>(const GraphView&, int, int, int64_t*, int64_t, cudaStream_t);

@@ -1,0 +1,67 @@
+"""The C ABI boundary on the CPU: the library builds for sm_103a, loads, and exports every
+entry point that include/nd.h declares; the binding wraps each of them. No kernel runs."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            names |= set(re.findall(r"^ND_API\s+[\w\s\*]*?\b(nd_\w+)\(", txt, flags=re.M))
+    return names
+
+
+def test_header_declares_the_north_star_calls():
+    names = declared_symbols()
+    for n in ["nd_load_csr", "nd_orient", "nd_count", "nd_decompose", "nd_ctx_create", "nd_last_error"]:
+        assert n in names
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    import paper_2111_10980_gb300 as nd
+    from paper_2111_10980_gb300 import build
+
+    path = build.build()
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (nd_\w+)$", out, flags=re.M))
+    missing = declared_symbols() - exported
+    assert not missing, f"declared but not exported: {sorted(missing)}"
+    # nothing but the declared API is exported
+    extra = {s for s in exported if s.startswith("nd_")} - declared_symbols()
+    assert not extra, f"exported but not declared: {sorted(extra)}"
+    L = nd.lib()
+    for name in declared_symbols():
+        assert hasattr(L, name)
+    assert set(nd.API) == declared_symbols()
+
+
+def test_built_for_sm_103a():
+    from paper_2111_10980_gb300 import build
+
+    path = build.build()
+    out = subprocess.run(["cuobjdump", "--list-elf", path], capture_output=True, text=True)
+    if out.returncode != 0:
+        pytest.skip("cuobjdump unavailable")
+    assert "sm_103a" in out.stdout
+
+
+def test_error_path_without_gpu():
+    """Argument errors are reported through nd_last_error without touching a device."""
+    import ctypes
+
+    import paper_2111_10980_gb300 as nd
+
+    L = nd.lib()
+    rc = L.nd_ctx_create(0, None, 0, None)
+    assert rc == nd.ND_EINVAL
+    assert "NULL" in nd.nd_last_error()
+    assert L.nd_graph_free(None) == nd.ND_OK
+    assert L.nd_orient(None, 0) == nd.ND_EINVAL
+    assert L.nd_decompose(None, 2, 3, 0, None, None, 0, None) == nd.ND_EINVAL
