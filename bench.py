@@ -77,6 +77,8 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--scale", type=int, default=None,
+                    help="R-MAT workload only: use scale S instead of 20 (profiling a smaller case)")
     return ap.parse_args()
 
 
@@ -241,8 +243,14 @@ def main():
     import paper_2111_10980_gb300 as nd
 
     torch.cuda.set_device(local)
-    wl = WORKLOADS[args.workload]
+    wl = dict(WORKLOADS[args.workload])
     width = wl.get("width", 0)
+    workload_name = args.workload
+    if args.scale is not None and args.workload == "rmat20":
+        sc = args.scale
+        wl["gen"] = lambda: gg.rmat(sc, 16, 0.57, 0.19, 0.19, seed=2)
+        wl["desc"] = wl["desc"].replace("scale 20", f"scale {sc}")
+        workload_name = f"rmat{sc}"
     g = wl["gen"]()
     stream = torch.cuda.Stream(device=local)
     ctx = nd.nd_ctx_create(local, stream=stream)
@@ -267,8 +275,8 @@ def main():
             stats[(r, s)] = st
         return stats
 
-    for _ in range(max(args.warmup, 1)):
-        stats = step()
+    for _ in range(args.warmup):
+        step()
 
     # timed region
     sampler = ClockSampler(gpu_uuid(local))
@@ -310,7 +318,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int64" if width == 8 else "int32", "data": "synthetic",
-            "config": {"workload": args.workload, "desc": wl["desc"], "n": g.n, "m": g.m,
+            "config": {"workload": workload_name, "desc": wl["desc"], "n": g.n, "m": g.m,
                        "rs": [f"({r},{s})" for r, s in wl["rs"]], "parallelism": f"replicas x{world}",
                        "l2": "flushed between steps (256 MiB write, outside the step events)"},
             "r_cliques_peeled_per_s": peeled_per_s,
