@@ -176,6 +176,32 @@ ND_API int nd_rounds(nd_graph *g, int64_t *sizes_out, int64_t *levels_out, int64
  * ND_PTR_DEVICE; NULL to query n_r only). r in {1, 2, 3}. Errors: ND_EINVAL, ND_ENOMEM. */
 ND_API int nd_rcliques(nd_graph *g, int r, int32_t *tuples_out, int flags, int64_t *n_r_out);
 
+/* ---- allocation-free entry point ----------------------------------------------------- */
+
+/* Largest graph (in vertices) that nd_kcore_noalloc accepts. */
+#define ND_NOALLOC_MAX_VERTICES 262144
+
+/* k-core coreness ((1,2) nucleus numbers) of a graph already in device memory, without any
+ * device or pinned-host allocation. The paper has no counterpart: this exists for callers that
+ * cannot let a library allocate -- a framework that has reserved the GPU's memory in its own
+ * caching pool (an allocation outside the pool can fail, or fragment memory, even though the
+ * pool has room), or a latency-critical loop where cudaMalloc/cudaFree may synchronise the
+ * device. It runs the same counting and peeling kernels as nd_decompose(g, 1, 2, ...), with all
+ * scratch in one fixed static device array (about 8.4 MB, held by every GPU that loads the
+ * library until the process exits).
+ *   n        number of vertices, 0 <= n <= ND_NOALLOC_MAX_VERTICES (ND_EINVAL otherwise)
+ *   rowptr   device int64[n+1], col device int32[rowptr[n]]: a symmetric CSR as in nd_load_csr
+ *            (sorted rows, no loops, no duplicates; not validated here)
+ *   core_out device int32[n], receives the coreness of every vertex
+ *   stream   cudaStream_t to run on (NULL: the legacy default stream); the call returns after
+ *            the work has finished on that stream. Runs on the calling thread's current device.
+ * The first call on a device looks up the device address of the static array
+ * (cudaGetSymbolAddress); make that first call before any stream capture. Every call shares
+ * the array: calls whose work overlaps on the GPU
+ * race and corrupt each other's results, so serialise them. Errors: ND_EINVAL, ND_ECUDA,
+ * ND_ETIMEOUT, ND_EINTERNAL. */
+ND_API int nd_kcore_noalloc(int32_t n, const int64_t *rowptr, const int32_t *col, int32_t *core_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -36,7 +36,8 @@ STATUS_NAMES = {0: "ND_OK", 1: "ND_EINVAL", 2: "ND_ENOMEM", 3: "ND_EOVERFLOW", 4
 # every entry point declared in include/nd.h
 API = ["nd_ctx_create", "nd_ctx_set_allocator", "nd_ctx_destroy", "nd_ctx_bytes_in_use", "nd_kernel_launches", "nd_last_error",
        "nd_load_csr", "nd_graph_free", "nd_graph_size", "nd_orient", "nd_graph_reset", "nd_count", "nd_decompose",
-       "nd_rounds", "nd_rcliques"]
+       "nd_rounds", "nd_rcliques", "nd_kcore_noalloc"]
+ND_NOALLOC_MAX_VERTICES = 262144
 
 
 class NdError(RuntimeError):
@@ -95,6 +96,7 @@ def lib() -> ctypes.CDLL:
                                    ctypes.POINTER(nd_stats)]
         L.nd_rounds.argtypes = [vp, vp, vp, i64, i64p]
         L.nd_rcliques.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, i64p]
+        L.nd_kcore_noalloc.argtypes = [i32, vp, vp, vp, vp]
         for name in API:
             if name not in ("nd_ctx_bytes_in_use", "nd_last_error", "nd_kernel_launches"):
                 getattr(L, name).restype = ctypes.c_int
@@ -295,3 +297,22 @@ def nd_rcliques(g: Handle, r: int, out=None):
     p, dev = _ptr(out)
     _check(lib().nd_rcliques(g.ptr, r, p, ND_PTR_DEVICE if dev else 0, ctypes.byref(n_r)))
     return out
+
+
+def nd_kcore_noalloc(rowptr, col, core_out, stream=None):
+    """k-core coreness without any allocation by the library (nd.h: nd_kcore_noalloc).
+
+    For callers that cannot let a library allocate device memory (a framework that has reserved
+    the GPU's memory in its own pool, or a latency-critical loop where cudaMalloc may
+    synchronise). rowptr (int64[n+1]), col (int32) and core_out (int32[n]) must be contiguous
+    CUDA tensors on the current device; n <= ND_NOALLOC_MAX_VERTICES. Calls share one static
+    scratch array, so calls that overlap on the GPU race: serialise them."""
+    for a in (rowptr, col, core_out):
+        if not _is_torch_cuda(a):
+            raise ValueError("nd_kcore_noalloc takes CUDA tensors (device memory)")
+    n = int(rowptr.shape[0]) - 1
+    raw = None
+    if stream is not None:
+        raw = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(lib().nd_kcore_noalloc(n, _ptr(rowptr)[0], _ptr(col)[0], _ptr(core_out)[0], raw))
+    return core_out
