@@ -335,6 +335,7 @@ typedef struct {
     int32_t R[8];
     int bad;
     int64_t listed;   /* s-cliques re-listed by Update */
+    int64_t live;     /* of those, the ones with no r-subset peeled in an earlier round */
 } update_ctx;
 
 /* Update-Func on the s-clique S = R u C (C is an (s-r)-clique in I). */
@@ -364,6 +365,7 @@ static void update_func(update_ctx *U, const int32_t *Cset) {
         int32_t rq = U->round[ids[q]];
         if (rq != U->t && rq >= 0) return;
     }
+    U->live++;
     /* subtract 1/a from every r-subset outside A (exactly: L/a on the scaled count) */
     for (int q = 0; q < nsub; ++q)
         if (U->round[ids[q]] != U->t) U->cnt[ids[q]] -= (i128)(U->L / a);
@@ -394,7 +396,7 @@ static void update_grow(update_ctx *U, int32_t *Cset, int depth, const int32_t *
  * Returns 0, -1 (bad r,s), -2 (no memory), -3 (internal inconsistency). */
 int orc_decompose(int32_t n, const int64_t *rp, const int32_t *col, int r, int s, int32_t *core, int32_t *round_out,
                   int64_t *rho_out, int64_t *sizes, int64_t *levels, int64_t cap, int64_t *n_s_out,
-                  int64_t *listed_out) {
+                  int64_t *listed_out, int64_t *live_out) {
     if (check_rs(r, s)) return -1;
     og g = {n, rp, col};
     rtable T;
@@ -500,6 +502,7 @@ int orc_decompose(int32_t n, const int64_t *rp, const int32_t *col, int r, int s
     if (round_out) memcpy(round_out, round, (size_t)nr * sizeof(int32_t));
     if (rho_out) *rho_out = t;
     if (listed_out) *listed_out = U.listed;
+    if (live_out) *live_out = U.live;
 done:
     free(c0);
     free(cnt);

@@ -265,6 +265,9 @@ def test_count_invariants(seed):
         assert int(d.sizes.sum()) == counts.size
         # every re-listing of Update is one (s-clique, member r-clique) pair
         assert d.listed == math.comb(s, r) * n_s
+        # an s-clique is live for the first round that peels any of its members, and for every
+        # member peeled in that round: at least n_s and at most the listings
+        assert n_s <= d.live <= d.listed
 
 
 def test_relabel_invariance():
