@@ -73,10 +73,17 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rmat20")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch", "serve"], default="rmat20")
+    ap.add_argument("--batch-graphs", type=int, default=4096)
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-pool", type=int, default=256)
+    ap.add_argument("--serve-workers", type=int, default=4)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--peel-mode", choices=["default", "persistent", "loop_graph", "plain"], default="default",
+                    help="how the peeling rounds are launched (default: the library's choice)")
     ap.add_argument("--scale", type=int, default=None,
                     help="R-MAT workload only: use scale S instead of 20 (profiling a smaller case)")
     return ap.parse_args()
@@ -243,6 +250,10 @@ def main():
     import paper_2111_10980_gb300 as nd
 
     torch.cuda.set_device(local)
+    if args.workload == "batch":
+        return run_batch(args, nd, world, rank, local, pg)
+    if args.workload == "serve":
+        return run_serve(args, nd, world, rank, local, pg)
     wl = dict(WORKLOADS[args.workload])
     width = wl.get("width", 0)
     workload_name = args.workload
@@ -261,6 +272,8 @@ def main():
     G = nd.nd_load_csr(ctx, rp_d, col_d)
 
     outs = {}
+    pflags = {"default": 0, "persistent": nd.ND_PEEL_PERSISTENT, "loop_graph": nd.ND_PEEL_LOOP_GRAPH,
+              "plain": nd.ND_NO_GRAPH}[args.peel_mode]
 
     def step():
         nd.nd_graph_reset(G)  # every step rebuilds orientation and indexes
@@ -268,10 +281,11 @@ def main():
         for r, s in wl["rs"]:
             core = outs.get((r, s))
             if core is None:  # first warm-up step: learn n_r, then keep a device output buffer
-                _, _, st = nd.nd_decompose(G, r, s, count_width=width, want_round=False)
+                _, _, st = nd.nd_decompose(G, r, s, count_width=width, want_round=False, flags=pflags)
                 outs[(r, s)] = torch.empty(max(st["n_r"], 1), dtype=torch.int32, device=f"cuda:{local}")
             else:
-                _, _, st = nd.nd_decompose(G, r, s, count_width=width, core_out=core, want_round=False)
+                _, _, st = nd.nd_decompose(G, r, s, count_width=width, core_out=core, want_round=False,
+                                           flags=pflags)
             stats[(r, s)] = st
         return stats
 
@@ -320,7 +334,8 @@ def main():
             "dtype": "int64" if width == 8 else "int32", "data": "synthetic",
             "config": {"workload": workload_name, "desc": wl["desc"], "n": g.n, "m": g.m,
                        "rs": [f"({r},{s})" for r, s in wl["rs"]], "parallelism": f"replicas x{world}",
-                       "l2": "flushed between steps (256 MiB write, outside the step events)"},
+                       "l2": "flushed between steps (256 MiB write, outside the step events)",
+                       "peel_mode": args.peel_mode},
             "r_cliques_peeled_per_s": peeled_per_s,
             "wall_s_timed": wall,
             "per_rs": {f"({r},{s})": {k: stats[(r, s)][k] for k in
@@ -427,6 +442,202 @@ def e2e(nd, wl, g, local, width, steps, world, pg):
     nd.nd_ctx_destroy(ctx)
     return {"value": units * steps * world / dt, "unit": "s-cliques/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "steps": steps}
+
+
+# ------------------------------------------------------------------------------------------
+# batched and served workloads
+
+def batch_graphs(count: int, seed: int = 4):
+    """count seeded Chung-Lu graphs: n ~ U[50, 5000], average degree ~ U[8, 40], exponent 2.2,
+    w_0 = min(sqrt(sum w), n - 1); (r,s) uniform over {(1,2), (2,3), (3,4)}."""
+    u = gg.uniform(seed, 3 * count)
+    rs = [(1, 2), (2, 3), (3, 4)]
+    out = []
+    for i in range(count):
+        n = 50 + int(u[3 * i] * 4951)
+        d = 8.0 + u[3 * i + 1] * 32.0
+        g = gg.chung_lu(n, d, 2.2, seed=seed + i, exact=False)
+        out.append((g, rs[min(2, int(u[3 * i + 2] * 3))]))
+    return out
+
+
+def run_batch(args, nd, world, rank, local, pg):
+    """Config: 4,096 small graphs of mixed (r,s), one nd_batch_run per batch, against one
+    load + decompose per graph (the plain path); host inputs and outputs in both."""
+    import numpy as np
+
+    items = batch_graphs(args.batch_graphs)
+    ctx = nd.nd_ctx_create(local)
+    graphs = [(g.rowptr, g.col, r, s) for g, (r, s) in items]
+    # output buffers sized once
+    outs, n_r, status, st0 = nd.nd_batch_run(ctx, graphs)
+    assert all(x == nd.ND_OK for x in status)
+    units = 0
+    n_s_of = []
+    for (g, (r, s)) in items:
+        G = nd.nd_load_csr(ctx, g.rowptr, g.col)
+        _, _, n_s = nd.nd_count(G, r, s)
+        nd.nd_graph_free(G)
+        n_s_of.append(n_s)
+        units += units_of(r, s, n_s)
+    bufs = [np.zeros(max(k, 1), np.int32) for k in n_r]
+    for _ in range(args.warmup):
+        nd.nd_batch_run(ctx, graphs, bufs)
+    launches0 = nd.nd_kernel_launches()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _, _, _, st = nd.nd_batch_run(ctx, graphs, bufs)
+    t_batch = (time.perf_counter() - t0) / args.steps
+    launches_batch = (nd.nd_kernel_launches() - launches0) // args.steps
+    # plain path: one graph at a time
+    t0 = time.perf_counter()
+    launches0 = nd.nd_kernel_launches()
+    for (g, (r, s)), b in zip(items, bufs):
+        G = nd.nd_load_csr(ctx, g.rowptr, g.col)
+        nd.nd_decompose(G, r, s, core_out=b, want_round=False)
+        nd.nd_graph_free(G)
+    t_plain = time.perf_counter() - t0
+    launches_plain = nd.nd_kernel_launches() - launches0
+    nd.nd_ctx_destroy(ctx)
+    t_batch = max_over_ranks(pg, t_batch, local)
+    t_plain = max_over_ranks(pg, t_plain, local)
+    line = {"metric": "batched (r,s) s-cliques/sec", "value": units * world / t_batch, "unit": "s-cliques/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t_batch,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": "batch", "graphs": len(items),
+                       "desc": "Chung-Lu graphs, n~U[50,5000], avg degree~U[8,40], exponent 2.2, "
+                               "(r,s) uniform over (1,2),(2,3),(3,4); host CSR in, host cores out",
+                       "m_total": int(sum(g.m for g, _ in items))},
+            "plain_one_graph_at_a_time": {"value": units * world / t_plain, "ms": 1000 * t_plain,
+                                          "gpu_launches": launches_plain},
+            "speedup_vs_plain": t_plain / t_batch, "gpu_launches": launches_batch,
+            "batch_stats": {k: st[k] for k in ("groups", "requests", "n_r_total", "n_s_total", "rho_max")}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def serve_pool(count: int, seed: int = 5):
+    """Graphs of the served stream: Chung-Lu or R-MAT with probability 1/2, edge count
+    log-uniform in [1e2, 1e6]; Chung-Lu with average degree ~U[8, 40], exponent 2.2, n = 2m/d;
+    R-MAT with n = 2^ceil(log2(m/8)) and Graph500 a, b, c."""
+    u = gg.uniform(seed, 3 * count)
+    out = []
+    for i in range(count):
+        m = int(round(math.exp(math.log(1e2) + u[3 * i] * (math.log(1e6) - math.log(1e2)))))
+        if u[3 * i + 1] < 0.5:
+            d = 8.0 + u[3 * i + 2] * 32.0
+            n = max(16, int(2 * m / d))
+            out.append(gg.chung_lu(n, d, 2.2, seed=seed * 100003 + i, exact=False))
+        else:
+            out.append(gg.rmat_m(m, seed=seed * 100003 + i))
+    return out
+
+
+def run_serve(args, nd, world, rank, local, pg):
+    """Config: a Poisson stream of requests against the continuous-batching server, compared
+    with serial one-at-a-time handling of the same trace on the same GPU."""
+    import threading
+
+    import numpy as np
+
+    pool = serve_pool(args.serve_pool)
+    rs_choices = [(2, 3), (3, 4), (2, 4)]
+    rng = np.random.default_rng(5 + rank)
+    horizon = args.serve_seconds
+    gaps = rng.exponential(1.0 / args.serve_rate, size=int(args.serve_rate * horizon * 1.2) + 16)
+    arrivals = np.cumsum(gaps)
+    arrivals = arrivals[arrivals < horizon]
+    picks = rng.integers(0, len(pool), size=arrivals.size)
+    rsi = rng.integers(0, 3, size=arrivals.size)
+    ctx = nd.nd_ctx_create(local)
+    # per (graph, rs): n_r, n_s and the plain service time (load + decompose + copy out)
+    info = {}
+    for gi, ri in set(zip(picks.tolist(), rsi.tolist())):
+        g = pool[gi]
+        r, s = rs_choices[ri]
+        G = nd.nd_load_csr(ctx, g.rowptr, g.col)
+        _, n_r, n_s = nd.nd_count(G, r, s)
+        nd.nd_graph_free(G)
+        info[(gi, ri)] = [n_r, n_s, 0.0]
+    for key in info:  # warm, then time each distinct request once
+        g = pool[key[0]]
+        r, s = rs_choices[key[1]]
+        for rep in range(2):
+            t0 = time.perf_counter()
+            G = nd.nd_load_csr(ctx, g.rowptr, g.col)
+            nd.nd_decompose(G, r, s, want_round=False)
+            nd.nd_graph_free(G)
+            info[key][2] = time.perf_counter() - t0
+    # serial FIFO on the same trace (Lindley recursion over measured service times)
+    lat_fifo = np.zeros(arrivals.size)
+    free_at = 0.0
+    for i in range(arrivals.size):
+        start = max(arrivals[i], free_at)
+        free_at = start + info[(int(picks[i]), int(rsi[i]))][2]
+        lat_fifo[i] = free_at - arrivals[i]
+    fifo_span = free_at
+    # live server
+    sv = nd.nd_server_create(ctx, workers=args.serve_workers, max_batch=256, queue_cap=1 << 20)
+    lat = []
+    done = threading.Event()
+    pending = {}
+    lock = threading.Lock()
+
+    def poller():
+        while not done.is_set() or pending:
+            with lock:
+                items = list(pending.items())
+            for t, _ in items:
+                rc, res = sv.poll(t)
+                if rc != nd.ND_PENDING:
+                    with lock:
+                        pending.pop(t, None)
+                    if rc == nd.ND_OK:
+                        lat.append(res["latency_ms"])
+            time.sleep(0.0005)
+
+    th = threading.Thread(target=poller, daemon=True)
+    th.start()
+    t0 = time.perf_counter()
+    rejected = 0
+    for i in range(arrivals.size):
+        wait = arrivals[i] - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        g = pool[int(picks[i])]
+        r, s = rs_choices[int(rsi[i])]
+        out = np.empty(max(info[(int(picks[i]), int(rsi[i]))][0], 1), np.int32)
+        try:
+            t = sv.submit(g.rowptr, g.col, r, s, out)
+            with lock:
+                pending[t] = True
+        except nd.NdError:
+            rejected += 1
+    done.set()
+    sv.drain()
+    th.join()
+    span = time.perf_counter() - t0
+    sv.close()
+    nd.nd_ctx_destroy(ctx)
+    units = sum(units_of(*rs_choices[int(rsi[i])], info[(int(picks[i]), int(rsi[i]))][1]) for i in range(arrivals.size))
+    lat = np.array(lat)
+    line = {"metric": "served (r,s) s-cliques/sec", "value": units * world / span, "unit": "s-cliques/s",
+            "n_gpus": world, "steps": 1, "warmup": 0, "ms_per_step": 1000 * span, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "serve", "rate_per_s": args.serve_rate, "seconds": horizon,
+                       "requests": int(arrivals.size), "pool_graphs": len(pool), "workers": args.serve_workers,
+                       "desc": "Poisson arrivals; graphs Chung-Lu or R-MAT, m log-uniform [1e2, 1e6], "
+                               "(r,s) uniform over (2,3),(3,4),(2,4); graphs pre-generated in host memory"},
+            "served": {"requests_per_s": len(lat) / span, "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
+                       "p99_ms": float(np.percentile(lat, 99)) if lat.size else None, "completed": int(lat.size),
+                       "rejected": rejected, "span_s": span},
+            "serial_fifo": {"requests_per_s": arrivals.size / fifo_span, "p50_ms": float(np.percentile(lat_fifo, 50) * 1000),
+                            "p99_ms": float(np.percentile(lat_fifo, 99) * 1000), "span_s": fifo_span}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
 
 
 if __name__ == "__main__":

@@ -60,7 +60,10 @@ extern "C" {
 /* ---- flags --------------------------------------------------------------------------- */
 #define ND_PTR_DEVICE 0x1 /* pointer arguments are device memory (default: host memory) */
 #define ND_VALIDATE 0x2   /* nd_load_csr: check the CSR invariants on the GPU */
-#define ND_NO_GRAPH 0x4   /* nd_decompose: launch the peeling rounds one by one, no CUDA graph */
+#define ND_NO_GRAPH 0x4   /* nd_decompose: launch every phase of every peeling round separately */
+#define ND_PEEL_LOOP_GRAPH 0x8  /* nd_decompose: run the peeling loop as one CUDA graph (WHILE/IF nodes) */
+#define ND_PEEL_PERSISTENT 0x10 /* nd_decompose: run the peeling loop as one cooperative kernel (default
+                                   when none of these three flags is given and the launch is possible) */
 
 /* ---- orientation modes (nd_orient) --------------------------------------------------- */
 #define ND_ORIENT_DEGREE 0     /* rank by (degree, id); out-degree <= sqrt(2m) */
@@ -175,6 +178,81 @@ ND_API int nd_rounds(nd_graph *g, int64_t *sizes_out, int64_t *levels_out, int64
  * ascending tuples of r int32 vertex ids in canonical order (host, or device with
  * ND_PTR_DEVICE; NULL to query n_r only). r in {1, 2, 3}. Errors: ND_EINVAL, ND_ENOMEM. */
 ND_API int nd_rcliques(nd_graph *g, int r, int32_t *tuples_out, int flags, int64_t *n_r_out);
+
+/* ---- batches and serving --------------------------------------------------------------
+ * Many independent graphs, each with its own (r,s). A batch merges the graphs that share an
+ * (r,s) into one disjoint union and runs a single decomposition on it: the core number of an
+ * r-clique depends only on its own connected component, so every graph gets exactly the
+ * numbers it would get alone, and the union's canonical order is the graphs' canonical orders
+ * one after another. All graphs of a batch are peeled in the same device-resident rounds. */
+
+typedef struct nd_request {
+    int32_t n;             /* vertices */
+    int32_t r, s;          /* a supported (r,s) */
+    const int64_t *rowptr; /* host int64[n+1]: symmetric CSR as in nd_load_csr */
+    const int32_t *col;    /* host int32[rowptr[n]] */
+    int32_t *core_out;     /* host int32[n_r] receiving the core numbers in canonical order, or
+                              NULL (only n_r is reported); caller-owned */
+    int64_t core_cap;      /* capacity of core_out in elements (checked; ND_EINVAL if too small) */
+    int64_t n_r;           /* out: number of r-cliques */
+    int32_t status;        /* out: ND_OK or this request's error */
+    int32_t pad;
+} nd_request;
+
+typedef struct nd_batch_stats {
+    int32_t groups;        /* distinct (r,s) in the batch = union decompositions run */
+    int32_t requests;
+    int64_t n_r_total, n_s_total;
+    int64_t rho_max;       /* most rounds of one union decomposition */
+    double t_total_ms;     /* wall time of the whole call, copies included */
+} nd_batch_stats;
+
+/* Decompose count requests (host CSRs, host outputs) as one batch per distinct (r,s) on the
+ * context's stream. Every request's status is set; the call returns ND_OK if all succeeded,
+ * else the first failing request's status (the others still complete). st may be NULL. */
+ND_API int nd_batch_run(nd_ctx *ctx, nd_request *reqs, int32_t count, nd_batch_stats *st);
+
+typedef struct nd_server nd_server;
+
+typedef struct nd_server_cfg {
+    size_t mem_budget;     /* device bytes that admitted requests may hold at once (0: no cap);
+                              admission uses a per-request estimate made before counting */
+    int32_t workers;       /* batches running on the device at once, each on its own stream (>= 1) */
+    int32_t max_batch;     /* most requests merged into one batch (>= 1) */
+    int32_t queue_cap;     /* most requests waiting for admission; nd_submit returns ND_EBUSY beyond */
+    int32_t pad;
+} nd_server_cfg;
+
+typedef struct nd_result {
+    int32_t status;        /* ND_PENDING while queued or running, else the request's final status */
+    int32_t batch_size;    /* requests in the batch that served it */
+    int64_t n_r;
+    double queue_ms;       /* nd_submit -> start of its batch */
+    double run_ms;         /* start -> results written */
+    double latency_ms;     /* nd_submit -> results written */
+} nd_result;
+
+/* Start a server on ctx's device: worker threads form batches from the queue (oldest request
+ * first, merging waiting requests with the same (r,s)), admit them while the memory budget
+ * allows, and run up to cfg->workers batches concurrently. Requests that arrive while batches
+ * are on the GPU join the next batch a worker forms. Errors: ND_EINVAL, ND_ECUDA. */
+ND_API int nd_server_create(nd_ctx *ctx, const nd_server_cfg *cfg, nd_server **out);
+
+/* Queue a request. Its arrays (rowptr, col, core_out) must stay valid and untouched until
+ * nd_poll reports a final status. *ticket identifies it. Errors: ND_EINVAL, ND_EBUSY (queue
+ * full), ND_ENOMEM (its estimate alone exceeds the budget). */
+ND_API int nd_submit(nd_server *sv, const nd_request *req, uint64_t *ticket);
+
+/* Status of a ticket: returns ND_PENDING while it is queued or running, else its final status
+ * (also in res->status) and, once final, forgets the ticket. res may be NULL.
+ * Errors: ND_EINVAL (unknown ticket). */
+ND_API int nd_poll(nd_server *sv, uint64_t ticket, nd_result *res);
+
+/* Block until every submitted request has finished (their results stay pollable). */
+ND_API int nd_server_drain(nd_server *sv);
+
+/* Finish all queued and running requests, stop the workers and free the server. */
+ND_API int nd_server_destroy(nd_server *sv);
 
 /* ---- allocation-free entry point ----------------------------------------------------- */
 

@@ -28,6 +28,8 @@ ND_OK, ND_EINVAL, ND_ENOMEM, ND_EOVERFLOW, ND_ETIMEOUT, ND_EBUSY, ND_PENDING, ND
 ND_PTR_DEVICE = 0x1
 ND_VALIDATE = 0x2
 ND_NO_GRAPH = 0x4
+ND_PEEL_LOOP_GRAPH = 0x8
+ND_PEEL_PERSISTENT = 0x10
 ND_ORIENT_DEGREE = 0
 ND_ORIENT_DEGENERACY = 1
 STATUS_NAMES = {0: "ND_OK", 1: "ND_EINVAL", 2: "ND_ENOMEM", 3: "ND_EOVERFLOW", 4: "ND_ETIMEOUT", 5: "ND_EBUSY",
@@ -36,7 +38,8 @@ STATUS_NAMES = {0: "ND_OK", 1: "ND_EINVAL", 2: "ND_ENOMEM", 3: "ND_EOVERFLOW", 4
 # every entry point declared in include/nd.h
 API = ["nd_ctx_create", "nd_ctx_set_allocator", "nd_ctx_destroy", "nd_ctx_bytes_in_use", "nd_kernel_launches", "nd_last_error",
        "nd_load_csr", "nd_graph_free", "nd_graph_size", "nd_orient", "nd_graph_reset", "nd_count", "nd_decompose",
-       "nd_rounds", "nd_rcliques", "nd_kcore_noalloc"]
+       "nd_rounds", "nd_rcliques", "nd_batch_run", "nd_server_create", "nd_submit", "nd_poll", "nd_server_drain",
+       "nd_server_destroy", "nd_kcore_noalloc"]
 ND_NOALLOC_MAX_VERTICES = 262144
 
 
@@ -52,6 +55,34 @@ class nd_stats(ctypes.Structure):
                 ("refills", ctypes.c_int64), ("count_width", ctypes.c_int32), ("orient_mode", ctypes.c_int32),
                 ("t_orient_ms", ctypes.c_double), ("t_index_ms", ctypes.c_double), ("t_count_ms", ctypes.c_double),
                 ("t_peel_ms", ctypes.c_double), ("t_total_ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class nd_request(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("r", ctypes.c_int32), ("s", ctypes.c_int32),
+                ("rowptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("core_out", ctypes.c_void_p),
+                ("core_cap", ctypes.c_int64), ("n_r", ctypes.c_int64), ("status", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
+
+
+class nd_batch_stats(ctypes.Structure):
+    _fields_ = [("groups", ctypes.c_int32), ("requests", ctypes.c_int32), ("n_r_total", ctypes.c_int64),
+                ("n_s_total", ctypes.c_int64), ("rho_max", ctypes.c_int64), ("t_total_ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class nd_server_cfg(ctypes.Structure):
+    _fields_ = [("mem_budget", ctypes.c_size_t), ("workers", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("queue_cap", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class nd_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("batch_size", ctypes.c_int32), ("n_r", ctypes.c_int64),
+                ("queue_ms", ctypes.c_double), ("run_ms", ctypes.c_double), ("latency_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -97,6 +128,12 @@ def lib() -> ctypes.CDLL:
         L.nd_rounds.argtypes = [vp, vp, vp, i64, i64p]
         L.nd_rcliques.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, i64p]
         L.nd_kcore_noalloc.argtypes = [i32, vp, vp, vp, vp]
+        L.nd_batch_run.argtypes = [vp, ctypes.POINTER(nd_request), i32, ctypes.POINTER(nd_batch_stats)]
+        L.nd_server_create.argtypes = [vp, ctypes.POINTER(nd_server_cfg), ctypes.POINTER(vp)]
+        L.nd_submit.argtypes = [vp, ctypes.POINTER(nd_request), ctypes.POINTER(ctypes.c_uint64)]
+        L.nd_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(nd_result)]
+        L.nd_server_drain.argtypes = [vp]
+        L.nd_server_destroy.argtypes = [vp]
         for name in API:
             if name not in ("nd_ctx_bytes_in_use", "nd_last_error", "nd_kernel_launches"):
                 getattr(L, name).restype = ctypes.c_int
@@ -316,3 +353,99 @@ def nd_kcore_noalloc(rowptr, col, core_out, stream=None):
         raw = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
     _check(lib().nd_kcore_noalloc(n, _ptr(rowptr)[0], _ptr(col)[0], _ptr(core_out)[0], raw))
     return core_out
+
+
+def _request(rowptr, col, r, s, core_out):
+    for a, dt in ((rowptr, np.int64), (col, np.int32)):
+        if not isinstance(a, np.ndarray) or a.dtype != dt or not a.flags.c_contiguous:
+            raise ValueError("batch/server requests take contiguous host arrays: rowptr int64, col int32")
+    q = nd_request()
+    q.n = int(rowptr.shape[0]) - 1
+    q.r, q.s = int(r), int(s)
+    q.rowptr = rowptr.ctypes.data
+    q.col = col.ctypes.data if col.size else None
+    if core_out is not None:
+        if core_out.dtype != np.int32 or not core_out.flags.c_contiguous:
+            raise ValueError("core_out must be a contiguous int32 numpy array")
+        q.core_out = core_out.ctypes.data
+        q.core_cap = int(core_out.shape[0])
+    return q
+
+
+def nd_batch_run(ctx: Handle, graphs, outs=None):
+    """Decompose a batch (nd.h: nd_batch_run). ``graphs`` is a list of (rowptr, col, r, s) with
+    host numpy arrays; ``outs`` an optional list of int32 arrays (one per graph, large enough).
+    Returns (outs, n_r list, status list, stats dict); allocates outputs when outs is None by
+    asking the library for each n_r first."""
+    k = len(graphs)
+    if outs is None:
+        reqs = (nd_request * k)(*[_request(rp, col, r, s, None) for rp, col, r, s in graphs])
+        st = nd_batch_stats()
+        lib().nd_batch_run(ctx.ptr, reqs, k, ctypes.byref(st))
+        outs = [np.zeros(max(int(reqs[i].n_r), 1), np.int32) for i in range(k)]
+    reqs = (nd_request * k)(*[_request(rp, col, r, s, o) for (rp, col, r, s), o in zip(graphs, outs)])
+    st = nd_batch_stats()
+    rc = lib().nd_batch_run(ctx.ptr, reqs, k, ctypes.byref(st))
+    n_r = [int(reqs[i].n_r) for i in range(k)]
+    status = [int(reqs[i].status) for i in range(k)]
+    if rc != ND_OK and all(x != ND_OK for x in status):
+        _check(rc)
+    return [o[:n] for o, n in zip(outs, n_r)], n_r, status, st.as_dict()
+
+
+class Server:
+    """A continuous-batching server (nd.h: nd_server_create / nd_submit / nd_poll)."""
+
+    def __init__(self, ctx: Handle, mem_budget: int = 0, workers: int = 2, max_batch: int = 64,
+                 queue_cap: int = 1 << 20):
+        cfg = nd_server_cfg(mem_budget, workers, max_batch, queue_cap, 0)
+        out = ctypes.c_void_p()
+        _check(lib().nd_server_create(ctx.ptr, ctypes.byref(cfg), ctypes.byref(out)))
+        self.ptr = out
+        self.keep = {}
+
+    def submit(self, rowptr, col, r, s, core_out):
+        q = _request(rowptr, col, r, s, core_out)
+        t = ctypes.c_uint64()
+        _check(lib().nd_submit(self.ptr, ctypes.byref(q), ctypes.byref(t)))
+        self.keep[t.value] = (rowptr, col, core_out)  # the library reads them until the final poll
+        return t.value
+
+    def poll(self, ticket):
+        res = nd_result()
+        rc = lib().nd_poll(self.ptr, ctypes.c_uint64(ticket), ctypes.byref(res))
+        if rc == ND_EINVAL and ticket not in self.keep:
+            _check(rc)
+        if rc != ND_PENDING:
+            self.keep.pop(ticket, None)
+        return rc, res.as_dict()
+
+    def drain(self):
+        _check(lib().nd_server_drain(self.ptr))
+
+    def close(self):
+        if self.ptr is not None:
+            _check(lib().nd_server_destroy(self.ptr))
+            self.ptr = None
+            self.keep.clear()
+
+
+def nd_server_create(ctx: Handle, mem_budget: int = 0, workers: int = 2, max_batch: int = 64,
+                     queue_cap: int = 1 << 20) -> Server:
+    return Server(ctx, mem_budget, workers, max_batch, queue_cap)
+
+
+def nd_submit(sv: Server, rowptr, col, r, s, core_out) -> int:
+    return sv.submit(rowptr, col, r, s, core_out)
+
+
+def nd_poll(sv: Server, ticket: int):
+    return sv.poll(ticket)
+
+
+def nd_server_drain(sv: Server):
+    sv.drain()
+
+
+def nd_server_destroy(sv: Server):
+    sv.close()

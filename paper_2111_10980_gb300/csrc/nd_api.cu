@@ -176,6 +176,8 @@ extern "C" int nd_ctx_destroy(nd_ctx* ctx) {
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    for (cudaStream_t x : ctx->cap_st)
+        if (x) cudaStreamDestroy(x);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     cudaGetLastError();
     delete ctx;
@@ -192,7 +194,7 @@ extern "C" int64_t nd_kernel_launches(void) { return nd_total_launches(); }
 static void free_derived(nd_graph* g) {
     nd_ctx* c = g->ctx;
     for (DBuf* b : {&g->split, &g->ebase, &g->pos2e, &g->eu, &g->ev, &g->dg_rp, &g->dg_col, &g->dg_eid, &g->et_rp,
-                    &g->et_w, &g->et_t, &g->tbase, &g->tri_e})
+                    &g->et_w, &g->et_t, &g->tbase, &g->tri_e, &g->tri_pos})
         nd_free(c, *b);
     g->have_base = false;
     g->orient = -1;
@@ -315,6 +317,8 @@ GraphView nd_view(const nd_graph* g) {
     v.et_t = (const int32_t*)g->et_t.p;
     v.tbase = (const int64_t*)g->tbase.p;
     v.tri_e = (const int32_t*)g->tri_e.p;
+    v.tri_pos = (const int32_t*)g->tri_pos.p;
+    v.et_flags = (int32_t*)g->et_t.p;
     v.n3 = g->n3;
     return v;
 }
@@ -451,17 +455,20 @@ static int ensure_tri(nd_graph* g) {
     int64_t n3 = tot[1];
     if (tot[0] != 3 * n3) return nd_set_error(ND_EINTERNAL, "triangle index: %lld entries for %lld triangles",
                                               (long long)tot[0], (long long)n3);
-    if (n3 > INT32_MAX) return nd_set_error(ND_EOVERFLOW, "%lld triangles: more than 2^31-1", (long long)n3);
+    // triangle ids share et_t with two flag bits (ND_ET_DEAD, ND_ET_INA)
+    if (n3 > (int64_t)ND_ET_ID)
+        return nd_set_error(ND_EOVERFLOW, "%lld triangles: more than 2^30-1", (long long)n3);
     if ((rc = nd_alloc(c, g->et_w, sizeof(int32_t) * std::max<int64_t>(3 * n3, 1))) ||
         (rc = nd_alloc(c, g->et_t, sizeof(int32_t) * std::max<int64_t>(3 * n3, 1))) ||
-        (rc = nd_alloc(c, g->tri_e, sizeof(int32_t) * std::max<int64_t>(3 * n3, 1))))
+        (rc = nd_alloc(c, g->tri_e, sizeof(int32_t) * std::max<int64_t>(3 * n3, 1))) ||
+        (rc = nd_alloc(c, g->tri_pos, sizeof(int32_t) * std::max<int64_t>(3 * n3, 1))))
         return rc;
     g->n3 = n3;
     v = nd_view(g);
     nd_edge_fill(v, (int64_t*)g->et_rp.p, (int64_t*)g->tbase.p, (int32_t*)g->et_w.p, (int32_t*)g->et_t.p,
-                 (int32_t*)g->tri_e.p, st);
+                 (int32_t*)g->tri_e.p, (int32_t*)g->tri_pos.p, st);
     v = nd_view(g);
-    nd_edge_fill_tid(v, (int32_t*)g->et_t.p, st);
+    nd_edge_fill_tid(v, (int32_t*)g->et_t.p, (int32_t*)g->tri_pos.p, st);
     ND_TRY(nd_check_launch("triangle index"));
     g->have_tri = true;
     return ND_OK;
@@ -596,12 +603,14 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
     cudaStream_t st = c->stream;
     int64_t cap = std::max<int64_t>(n_r, 1);
     int64_t rcap = std::min<int64_t>(n_r, (int64_t)1 << 22) + 1;
-    DBuf ctl, A0, A1, N0, N1, L0, L1, rs, rl;
+    int64_t hcap = std::min<int64_t>(cap, (int64_t)1 << 20);
+    DBuf ctl, A0, A1, N0, N1, L0, L1, H, rs, rl;
     int rc = ND_OK;
     if ((rc = nd_alloc(c, ctl, sizeof(PeelCtl))) || (rc = nd_alloc(c, A0, 4 * cap)) || (rc = nd_alloc(c, A1, 4 * cap)) ||
         (rc = nd_alloc(c, N0, 4 * cap)) || (rc = nd_alloc(c, N1, 4 * cap)) || (rc = nd_alloc(c, L0, 4 * cap)) ||
-        (rc = nd_alloc(c, L1, 4 * cap)) || (rc = nd_alloc(c, rs, 8 * rcap)) || (rc = nd_alloc(c, rl, 8 * rcap))) {
-        for (DBuf* b : {&ctl, &A0, &A1, &N0, &N1, &L0, &L1, &rs, &rl}) nd_free(c, *b);
+        (rc = nd_alloc(c, L1, 4 * cap)) || (rc = nd_alloc(c, H, 4 * hcap)) || (rc = nd_alloc(c, rs, 8 * rcap)) ||
+        (rc = nd_alloc(c, rl, 8 * rcap))) {
+        for (DBuf* b : {&ctl, &A0, &A1, &N0, &N1, &L0, &L1, &H, &rs, &rl}) nd_free(c, *b);
         return rc;
     }
     PeelView<CT> P;
@@ -614,6 +623,8 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
     P.N[1] = (int32_t*)N1.p;
     P.L[0] = (int32_t*)L0.p;
     P.L[1] = (int32_t*)L1.p;
+    P.H = (int32_t*)H.p;
+    P.hcap = (uint32_t)hcap;
     P.cap = (uint32_t)cap;
     P.ctl = (PeelCtl*)ctl.p;
     P.round_size = (int64_t*)rs.p;
@@ -623,12 +634,49 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
     nd_fill_i32(P.core, 0, n_r, st);
     nd_peel_init(P.ctl, n_r, n_r + 2, st);
     GraphView v = nd_view(g);
+    if (r == 3) nd_edge_clear_flags(v, st);  // flags of a previous (3,4) peel on this graph
+    bool looped = false;
+    int persistent_launches = 0;
+    bool want_persistent = (flags & ND_PEEL_PERSISTENT) || !(flags & (ND_NO_GRAPH | ND_PEEL_LOOP_GRAPH));
+    if (want_persistent) {
+        // preferred: the whole loop in one cooperative kernel
+        cudaError_t e = nd_peel_persistent<CT>(v, r, s, P, st);
+        if (e == cudaSuccess) {
+            looped = true;
+            persistent_launches = 1;
+            rc = nd_sync(c, "peel (persistent)");
+        } else {
+            cudaGetLastError();
+            if (flags & ND_PEEL_PERSISTENT)
+                rc = nd_set_error(ND_ECUDA, "cooperative launch of the peel loop failed: %s", cudaGetErrorString(e));
+        }
+    }
+    if (!looped && !rc && !(flags & ND_NO_GRAPH)) {
+        // preferred: the whole loop in one graph launch (WHILE / IF conditional nodes)
+        for (int i = 0; i < 2; ++i)
+            if (!c->cap_st[i] && cudaStreamCreateWithFlags(&c->cap_st[i], cudaStreamNonBlocking) != cudaSuccess) {
+                cudaGetLastError();
+                c->cap_st[i] = nullptr;
+            }
+        cudaGraph_t lg = nullptr;
+        cudaGraphExec_t lx = nullptr;
+        if (c->cap_st[0] && c->cap_st[1] &&
+            nd_peel_loop_graph<CT>(v, r, s, P, st, c->cap_st[0], c->cap_st[1], &lg) == cudaSuccess &&
+            cudaGraphInstantiate(&lx, lg, 0) == cudaSuccess) {
+            looped = true;
+            rc = (cudaGraphLaunch(lx, st) == cudaSuccess) ? ND_OK : nd_check_launch("peel loop graph");
+            if (!rc) rc = nd_sync(c, "peel loop graph");
+        }
+        cudaGetLastError();
+        if (lx) cudaGraphExecDestroy(lx);
+        if (lg) cudaGraphDestroy(lg);
+    }
     const int kChunk = 32;
     int64_t max_chunks = (n_r + 2) / kChunk + 4;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     size_t graph_nodes = 0;
-    bool use_graph = !(flags & ND_NO_GRAPH);
+    bool use_graph = !(flags & ND_NO_GRAPH) && !looped && !rc;
     if (use_graph) {
         cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
@@ -648,9 +696,9 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
         }
     }
     int32_t* hdone = (int32_t*)c->pinned;
-    rc = ND_OK;
     int64_t chunks = 0;
-    for (;;) {
+    if (looped) use_graph = false;
+    for (; !looped && !rc;) {
         if (use_graph) {
             cudaGraphLaunch(exec, st);
             nd_note_launches((int64_t)graph_nodes);
@@ -674,13 +722,17 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
         rc = nd_sync(c, "peel stats");
         if (!rc) {
             memcpy(&h, c->pinned, std::min<size_t>(sizeof(PeelCtl), 4096));
-            if (h.err & 1) rc = nd_set_error(ND_EINTERNAL, "peel: a work list overflowed");
+            if (h.err & 8) rc = nd_set_error(ND_ETIMEOUT, "peel: a grid barrier of the persistent kernel timed out");
+            else if (h.err & 1) rc = nd_set_error(ND_EINTERNAL, "peel: a work list overflowed");
             else if (h.err & 2) rc = nd_set_error(ND_ETIMEOUT, "peel: round cap reached");
             else if (h.err & 4) rc = nd_set_error(ND_EINTERNAL, "peel: empty round (inconsistent state)");
             else if (h.finished != n_r) rc = nd_set_error(ND_EINTERNAL, "peel: finished %lld of %lld",
                                                           (long long)h.finished, (long long)n_r);
             po.rho = h.t;
             po.max_core = n_r ? h.k : 0;
+            if (looped && !persistent_launches)  // graph nodes executed: every iteration (rho + 1), plus advance and refill phases
+                nd_note_launches((int64_t)(h.t + 1) * nd_peel_nodes_per_round(r, s) + 3 * (int64_t)h.advances +
+                                 4 * (int64_t)h.refills);
             po.listed = (int64_t)h.listed;
             po.advances = h.advances;
             po.refills = h.refills;
@@ -697,7 +749,7 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
             rc = nd_sync(c, "peel record");
         }
     }
-    for (DBuf* b : {&ctl, &A0, &A1, &N0, &N1, &L0, &L1, &rs, &rl}) nd_free(c, *b);
+    for (DBuf* b : {&ctl, &A0, &A1, &N0, &N1, &L0, &L1, &H, &rs, &rl}) nd_free(c, *b);
     return rc;
 }
 

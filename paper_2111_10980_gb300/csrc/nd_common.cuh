@@ -13,12 +13,18 @@
 //                        et_t int32[3 n3]  canonical id of triangle {a,b,w} per entry
 //                        tbase int64[m+1]  exclusive scan of |{w in L(a,b) : w > b}|
 //                        tri_e int32[3 n3] edges (ab, ac, bc) of triangle (a<b<c)
+//                        tri_pos int32[3 n3] offset of the triangle's entry in L(ab), L(ac), L(bc)
+//   During a (3,4) peel the two top bits of et_t flag the entry's triangle: ND_ET_DEAD (peeled
+//   in an earlier round) and ND_ET_INA (in the current round's A); ids therefore stay < 2^30.
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #define ND_UNPEELED 0x7fffffff
+#define ND_ET_DEAD 0x80000000u
+#define ND_ET_INA 0x40000000u
+#define ND_ET_ID 0x3fffffffu
 #define ND_WARP 32
 
 // ------------------------------------------------------------------------------------
@@ -98,6 +104,8 @@ struct GraphView {
     const int32_t* et_t;
     const int64_t* tbase;
     const int32_t* tri_e;
+    const int32_t* tri_pos;
+    int32_t* et_flags;  // et_t, writable view for the (3,4) peel's flag bits
     int64_t n3;
 };
 
@@ -130,9 +138,11 @@ struct PeelCtl {
     unsigned int nN2;   // |N'| being written this round (advance rounds)
     unsigned int nL;    // |L|
     unsigned int nL2;   // |L'| being written by refill
-    unsigned int pad1;
+    unsigned int nH;    // r-cliques of this round's A deferred to the heavy Update kernel
     unsigned long long minN;  // min count over unpeeled members of N (adv_min)
     unsigned long long gmin;  // min count over unpeeled r-cliques (refill)
+    // grid barrier of the persistent peel kernel (arrivals since the launch)
+    unsigned long long bar_arrive;
     // statistics
     unsigned long long listed;
     long long advances, refills;
@@ -147,6 +157,8 @@ struct PeelView {
     int32_t* A[2];
     int32_t* N[2];
     int32_t* L[2];
+    int32_t* H;      // heavy r-cliques of the current round (capacity hcap)
+    uint32_t hcap;
     uint32_t cap;
     PeelCtl* ctl;
     int64_t* round_size;
@@ -192,8 +204,9 @@ void nd_dg_fill(const GraphView& g, const int32_t* key_hi, int64_t* dg_rp_in, in
 // per canonical edge: sigma = |N(a) ∩ N(b)|, up = |{w in N(a) ∩ N(b) : w > b}|
 void nd_edge_support(const GraphView& g, int64_t* sigma, int64_t* up, cudaStream_t st);
 void nd_edge_fill(const GraphView& g, int64_t* et_rp, int64_t* tbase, int32_t* et_w, int32_t* et_t,
-                  int32_t* tri_e, cudaStream_t st);
-void nd_edge_fill_tid(const GraphView& g, int32_t* et_t, cudaStream_t st);
+                  int32_t* tri_e, int32_t* tri_pos, cudaStream_t st);
+void nd_edge_fill_tid(const GraphView& g, int32_t* et_t, int32_t* tri_pos, cudaStream_t st);
+void nd_edge_clear_flags(const GraphView& g, cudaStream_t st);
 void nd_tri_tuples(const GraphView& g, int32_t* out, cudaStream_t st);
 void nd_edge_tuples(const GraphView& g, int32_t* out, cudaStream_t st);
 
@@ -204,6 +217,15 @@ void nd_count_launch(const GraphView& g, int r, int s, CT* cnt, int64_t n_r, cud
 // peeling (nd_peel.cu)
 template <typename CT>
 void nd_peel_round(const GraphView& g, int r, int s, const PeelView<CT>& P, cudaStream_t st);
+// the whole loop as one graph (WHILE node over rounds, IF nodes for the advance and refill
+// phases); st2 and st3 are extra streams used only while capturing
+template <typename CT>
+cudaError_t nd_peel_loop_graph(const GraphView& g, int r, int s, const PeelView<CT>& P, cudaStream_t st,
+                               cudaStream_t st2, cudaStream_t st3, cudaGraph_t* out);
+int nd_peel_nodes_per_round(int r, int s);
+// the whole loop as one cooperative kernel launch
+template <typename CT>
+cudaError_t nd_peel_persistent(const GraphView& g, int r, int s, const PeelView<CT>& P, cudaStream_t st);
 void nd_peel_init(PeelCtl* ctl, int64_t n_r, int64_t max_rounds, cudaStream_t st);
 
 int nd_sm_count();

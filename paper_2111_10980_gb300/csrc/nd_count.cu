@@ -63,7 +63,8 @@ __global__ void k_count23(GraphView g, CT* __restrict__ cnt) {
     }
 }
 
-// count[t] = |L(ab) ∩ L(ac) ∩ L(bc)|
+// count[t] = |L(ab) ∩ L(ac) ∩ L(bc)|. Any two of the lists already intersect to the common
+// neighbourhood of the triangle (L(ab) ∩ L(ac) = N(a) ∩ N(b) ∩ N(c)), so the two shortest suffice.
 template <typename CT>
 __global__ void k_count34(GraphView g, CT* __restrict__ cnt) {
     int lane = threadIdx.x & 31;
@@ -72,7 +73,7 @@ __global__ void k_count34(GraphView g, CT* __restrict__ cnt) {
         int64_t b0 = g.et_rp[e0], n0 = g.et_rp[e0 + 1] - b0;
         int64_t b1 = g.et_rp[e1], n1 = g.et_rp[e1 + 1] - b1;
         int64_t b2 = g.et_rp[e2], n2 = g.et_rp[e2 + 1] - b2;
-        // drive with the shortest list
+        // the two shortest lists: (b0, n0) drives, (b1, n1) is searched
         if (n1 < n0) {
             int64_t tb = b0, tn = n0;
             b0 = b1, n0 = n1, b1 = tb, n1 = tn;
@@ -81,11 +82,9 @@ __global__ void k_count34(GraphView g, CT* __restrict__ cnt) {
             int64_t tb = b0, tn = n0;
             b0 = b2, n0 = n2, b2 = tb, n2 = tn;
         }
+        if (n2 < n1) b1 = b2, n1 = n2;
         int c = 0;
-        for (int64_t i = lane; i < n0; i += 32) {
-            int32_t w = g.et_w[b0 + i];
-            if (nd_find(g.et_w + b1, n1, w) >= 0 && nd_find(g.et_w + b2, n2, w) >= 0) c++;
-        }
+        for (int64_t i = lane; i < n0; i += 32) c += nd_find(g.et_w + b1, n1, g.et_w[b0 + i]) >= 0 ? 1 : 0;
         c = warp_sum(c);
         if (lane == 0) cnt[t] = (CT)c;
     }

@@ -181,7 +181,8 @@ __global__ void k_edge_support(GraphView g, int64_t* __restrict__ sigma, int64_t
 // Writes L(a,b) in ascending w with, per entry: the canonical triangle id when w > b, else
 // (temporarily) the id of edge (a,w); and the edges of every triangle whose lowest edge is e.
 __global__ void k_edge_fill(GraphView g, const int64_t* __restrict__ et_rp, const int64_t* __restrict__ tbase,
-                            int32_t* __restrict__ et_w, int32_t* __restrict__ et_t, int32_t* __restrict__ tri_e) {
+                            int32_t* __restrict__ et_w, int32_t* __restrict__ et_t, int32_t* __restrict__ tri_e,
+                            int32_t* __restrict__ tri_pos) {
     int lane = threadIdx.x & 31;
     for (int64_t e = gwarp(); e < g.m; e += nwarps()) {
         int32_t a = g.eu[e], b = g.ev[e];
@@ -215,6 +216,7 @@ __global__ void k_edge_fill(GraphView g, const int64_t* __restrict__ et_rp, cons
                     tri_e[3 * tid + 0] = (int32_t)e;
                     tri_e[3 * tid + 1] = e_aw;
                     tri_e[3 * tid + 2] = e_bw;
+                    tri_pos[3 * tid + 0] = (int32_t)local;
                 } else {
                     et_t[out + local] = e_aw;
                 }
@@ -226,10 +228,11 @@ __global__ void k_edge_fill(GraphView g, const int64_t* __restrict__ et_rp, cons
 
 // For entries of L(a,b) with w < b, the triangle {a,w,b} has b as its largest vertex, so its
 // lowest edge is (a,w) (or (w,a)); its id is tbase[e'] + rank of b among the upper entries of L(e').
-__global__ void k_edge_fill_tid(GraphView g, int32_t* __restrict__ et_t) {
+// The entry is the triangle's (a,c) entry when a < w, its (b,c) entry when w < a (slots 1, 2).
+__global__ void k_edge_fill_tid(GraphView g, int32_t* __restrict__ et_t, int32_t* __restrict__ tri_pos) {
     int lane = threadIdx.x & 31;
     for (int64_t e = gwarp(); e < g.m; e += nwarps()) {
-        int32_t b = g.ev[e];
+        int32_t a = g.eu[e], b = g.ev[e];
         int64_t lo = g.et_rp[e], hi = g.et_rp[e + 1];
         int64_t split_e = (hi - lo) - (g.tbase[e + 1] - g.tbase[e]);
         for (int64_t j = lo + lane; j < lo + split_e; j += 32) {
@@ -237,9 +240,16 @@ __global__ void k_edge_fill_tid(GraphView g, int32_t* __restrict__ et_t) {
             int64_t l2 = g.et_rp[e2], h2 = g.et_rp[e2 + 1];
             int64_t s2 = (h2 - l2) - (g.tbase[e2 + 1] - g.tbase[e2]);
             int64_t at = nd_lower_bound(g.et_w + l2, h2 - l2, b);
-            et_t[j] = (int32_t)(g.tbase[e2] + (at - s2));
+            int64_t tid = g.tbase[e2] + (at - s2);
+            et_t[j] = (int32_t)tid;
+            tri_pos[3 * tid + (g.et_w[j] > a ? 1 : 2)] = (int32_t)(j - lo);
         }
     }
+}
+
+__global__ void k_clear_flags(int32_t* __restrict__ et_t, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        et_t[i] = (int32_t)((uint32_t)et_t[i] & ND_ET_ID);
 }
 
 __global__ void k_tri_tuples(GraphView g, int32_t* __restrict__ out) {
@@ -293,14 +303,19 @@ void nd_edge_support(const GraphView& g, int64_t* sigma, int64_t* up, cudaStream
 }
 
 void nd_edge_fill(const GraphView& g, int64_t* et_rp, int64_t* tbase, int32_t* et_w, int32_t* et_t, int32_t* tri_e,
-                  cudaStream_t st) {
+                  int32_t* tri_pos, cudaStream_t st) {
     if (g.m <= 0) return;
-    ND_K(k_edge_fill<<<blocks_for_warps(g.m), kThreads, 0, st>>>(g, et_rp, tbase, et_w, et_t, tri_e));
+    ND_K(k_edge_fill<<<blocks_for_warps(g.m), kThreads, 0, st>>>(g, et_rp, tbase, et_w, et_t, tri_e, tri_pos));
 }
 
-void nd_edge_fill_tid(const GraphView& g, int32_t* et_t, cudaStream_t st) {
+void nd_edge_fill_tid(const GraphView& g, int32_t* et_t, int32_t* tri_pos, cudaStream_t st) {
     if (g.m <= 0) return;
-    ND_K(k_edge_fill_tid<<<blocks_for_warps(g.m), kThreads, 0, st>>>(g, et_t));
+    ND_K(k_edge_fill_tid<<<blocks_for_warps(g.m), kThreads, 0, st>>>(g, et_t, tri_pos));
+}
+
+void nd_edge_clear_flags(const GraphView& g, cudaStream_t st) {
+    if (g.n3 <= 0) return;
+    ND_K(k_clear_flags<<<blocks_for_threads(3 * g.n3), kThreads, 0, st>>>(g.et_flags, 3 * g.n3));
 }
 
 void nd_tri_tuples(const GraphView& g, int32_t* out, cudaStream_t st) {

@@ -26,6 +26,7 @@ struct nd_ctx {
     nd_free_fn ff = nullptr;
     void* user = nullptr;
     void* pinned = nullptr;  // 4 KiB of pinned host memory for scalar read-backs
+    cudaStream_t cap_st[2] = {nullptr, nullptr};  // extra streams used only to capture graph bodies
 };
 
 struct nd_graph {
@@ -45,7 +46,7 @@ struct nd_graph {
     // triangle index
     bool have_tri = false;
     int64_t n3 = 0;
-    DBuf et_rp, et_w, et_t, tbase, tri_e;
+    DBuf et_rp, et_w, et_t, tbase, tri_e, tri_pos;
     // record of the last decomposition
     bool have_last = false;
     int64_t last_rho = 0;

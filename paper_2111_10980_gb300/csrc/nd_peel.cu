@@ -34,6 +34,7 @@
 #include "nd_common.cuh"
 
 #include <climits>
+#include <cstring>
 
 namespace {
 
@@ -49,6 +50,10 @@ __device__ __forceinline__ int64_t knew_of(const PeelCtl* c) {
     int64_t m = mn == ULLONG_MAX ? c->k : (int64_t)mn;
     return m > c->k ? m : c->k;
 }
+
+// a[i] for a two-entry pointer array without dynamic indexing (which would copy the kernel
+// parameter block to local memory)
+__device__ __forceinline__ int32_t* pick(int32_t* const (&a)[2], int i) { return i ? a[1] : a[0]; }
 
 // list sizes read back from the control block never exceed the list capacity (an overflow sets
 // ctl->err and is reported by the host)
@@ -91,16 +96,35 @@ __global__ void k_init(PeelCtl* c, int64_t n_r, int64_t max_rounds) {
         c->finished = 0;
         c->n_r = n_r;
         c->max_rounds = max_rounds;
-        c->nA = c->cntA = c->nNext = c->nN = c->nN2 = c->nL = c->nL2 = 0;
+        c->nA = c->cntA = c->nNext = c->nN = c->nN2 = c->nL = c->nL2 = c->nH = 0;
         c->minN = c->gmin = ULLONG_MAX;
         c->listed = 0;
+        c->bar_arrive = 0;
         c->advances = c->refills = 0;
     }
 }
 
-// Finishes round t-1 and sets up round t (one thread).
-__global__ void k_ctl(PeelCtl* c, int64_t* round_size, int64_t* round_level, int64_t round_cap) {
+// Finishes round t-1 and sets up round t (one thread). When the rounds run inside a CUDA graph
+// WHILE node, it also sets the loop condition (continue while not done) and the IF condition of
+// the level-advance phase.
+__device__ void ctl_step(PeelCtl* c, int64_t* round_size, int64_t* round_level, int64_t round_cap);
+
+__global__ void k_ctl(PeelCtl* c, int64_t* round_size, int64_t* round_level, int64_t round_cap, int use_cond,
+                      cudaGraphConditionalHandle h_loop, cudaGraphConditionalHandle h_adv) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    ctl_step(c, round_size, round_level, round_cap);
+    if (use_cond) {
+        cudaGraphSetConditional(h_loop, c->done ? 0u : 1u);
+        cudaGraphSetConditional(h_adv, (!c->done && (c->mode & ND_MODE_ADV)) ? 1u : 0u);
+    }
+}
+
+// IF condition of the refill phase: the window N holds no unpeeled r-clique
+__global__ void k_set_refill(PeelCtl* c, cudaGraphConditionalHandle h_refill) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(h_refill, need_refill(c) ? 1u : 0u);
+}
+
+__device__ void ctl_step(PeelCtl* c, int64_t* round_size, int64_t* round_level, int64_t round_cap) {
     if (c->done) return;
     if (c->started) {
         bool adv = c->mode & ND_MODE_ADV;
@@ -138,6 +162,7 @@ __global__ void k_ctl(PeelCtl* c, int64_t* round_size, int64_t* round_level, int
             return;
         }
     }
+    c->nH = 0;
     if (c->nNext > 0) {
         c->wa ^= 1;
         c->nA = c->nNext;
@@ -154,10 +179,10 @@ __global__ void k_ctl(PeelCtl* c, int64_t* round_size, int64_t* round_level, int
 }
 
 template <typename CT>
-__global__ void k_adv_min(PeelView<CT> P) {
+__device__ void phase_adv_min(const PeelView<CT>& P) {
     PeelCtl* c = P.ctl;
     if (c->done || !(c->mode & ND_MODE_ADV)) return;
-    const int32_t* N = P.N[c->wn];
+    const int32_t* N = pick(P.N, c->wn);
     unsigned n = clampn(c->nN, P.cap);
     unsigned long long mn = ULLONG_MAX;
     for (int64_t i = gthread(); i < n; i += nthreads()) {
@@ -173,12 +198,12 @@ __global__ void k_adv_min(PeelView<CT> P) {
 
 // refill 1/4: compact L into L' (alive only), global minimum count, clear the histogram
 template <typename CT>
-__global__ void k_refill_scan(PeelView<CT> P) {
+__device__ void phase_refill_scan(const PeelView<CT>& P) {
     PeelCtl* c = P.ctl;
     if (!need_refill(c)) return;
     for (int64_t i = gthread(); i < ND_HBINS; i += nthreads()) c->hist[i] = 0;
-    const int32_t* L = P.L[c->wl];
-    int32_t* L2 = P.L[c->wl ^ 1];
+    const int32_t* L = pick(P.L, c->wl);
+    int32_t* L2 = pick(P.L, c->wl ^ 1);
     int64_t n = c->lmat ? (int64_t)clampn(c->nL, P.cap) : c->n_r;
     unsigned long long mn = ULLONG_MAX;
     // grid-stride in whole-warp steps so that appends aggregate per warp
@@ -199,13 +224,13 @@ __global__ void k_refill_scan(PeelView<CT> P) {
 
 // refill 2/4: histogram of count - gmin over L'
 template <typename CT>
-__global__ void k_refill_hist(PeelView<CT> P) {
+__device__ void phase_refill_hist(const PeelView<CT>& P) {
     PeelCtl* c = P.ctl;
     if (!need_refill(c)) return;
     __shared__ unsigned int h[ND_HBINS];
     for (int i = threadIdx.x; i < ND_HBINS; i += blockDim.x) h[i] = 0;
     __syncthreads();
-    const int32_t* L2 = P.L[c->wl ^ 1];
+    const int32_t* L2 = pick(P.L, c->wl ^ 1);
     unsigned n = clampn(c->nL2, P.cap);
     unsigned long long g0 = c->gmin;
     for (int64_t i = gthread(); i < n; i += nthreads()) {
@@ -217,19 +242,21 @@ __global__ void k_refill_hist(PeelView<CT> P) {
         if (h[i]) atomicAdd(&c->hist[i], (unsigned long long)h[i]);
 }
 
-// refill 3/4 (one block of 1024): choose hi, swap L <- L', clear N
-__global__ void k_refill_pick(PeelCtl* c) {
+// refill 3/4 (one block; any multiple of 32 threads dividing ND_HBINS): choose hi so that the
+// window holds about 1/16 of the unpeeled r-cliques (at least 16384), swap L <- L', clear N
+__device__ void phase_refill_pick(PeelCtl* c) {
     if (!need_refill(c)) return;
     __shared__ unsigned long long part[1024];
     __shared__ int best;
-    constexpr int per = ND_HBINS / 1024;
+    const int nt = blockDim.x;
+    const int per = ND_HBINS / nt;
     unsigned long long s = 0;
     for (int j = 0; j < per; ++j) s += c->hist[threadIdx.x * per + j];
     part[threadIdx.x] = s;
     if (threadIdx.x == 0) best = ND_HBINS - 1;
     __syncthreads();
-    // inclusive scan of part (Hillis-Steele; 1024 entries)
-    for (int o = 1; o < 1024; o <<= 1) {
+    // inclusive scan of part[0..nt) (Hillis-Steele)
+    for (int o = 1; o < nt; o <<= 1) {
         unsigned long long y = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
         __syncthreads();
         part[threadIdx.x] += y;
@@ -238,8 +265,7 @@ __global__ void k_refill_pick(PeelCtl* c) {
     unsigned long long alive = c->nL2;
     unsigned long long target = alive / 16;
     if (target < 16384) target = 16384;
-    unsigned long long before = threadIdx.x ? part[threadIdx.x - 1] : 0;
-    unsigned long long run = before;
+    unsigned long long run = threadIdx.x ? part[threadIdx.x - 1] : 0;
     for (int j = 0; j < per; ++j) {
         run += c->hist[threadIdx.x * per + j];
         if (run >= target) {
@@ -258,15 +284,18 @@ __global__ void k_refill_pick(PeelCtl* c) {
         c->nN = 0;
         c->refills++;
     }
+    __syncthreads();
 }
+
+__global__ void k_refill_pick(PeelCtl* c) { phase_refill_pick(c); }
 
 // refill 4/4: N = { R in L : count < hi }
 template <typename CT>
-__global__ void k_refill_select(PeelView<CT> P) {
+__device__ void phase_refill_select(const PeelView<CT>& P) {
     PeelCtl* c = P.ctl;
     if (!need_refill(c)) return;
-    const int32_t* L = P.L[c->wl];
-    int32_t* N = P.N[c->wn];
+    const int32_t* L = pick(P.L, c->wl);
+    int32_t* N = pick(P.N, c->wn);
     unsigned n = clampn(c->nL, P.cap);
     int64_t hi = c->hi;
     for (int64_t base = gthread() - (threadIdx.x & 31); base < n; base += nthreads()) {
@@ -280,13 +309,13 @@ __global__ void k_refill_select(PeelView<CT> P) {
 
 // advance: k' = max(k, min over N); A = { R in N alive : count <= k' }; N' = the other alive
 template <typename CT>
-__global__ void k_adv_select(PeelView<CT> P) {
+__device__ void phase_adv_select(const PeelView<CT>& P) {
     PeelCtl* c = P.ctl;
     if (c->done || !(c->mode & ND_MODE_ADV)) return;
     int64_t kn = knew_of(c);
-    const int32_t* N = P.N[c->wn];
-    int32_t* N2 = P.N[c->wn ^ 1];
-    int32_t* A = P.A[c->wa];
+    const int32_t* N = pick(P.N, c->wn);
+    int32_t* N2 = pick(P.N, c->wn ^ 1);
+    int32_t* A = pick(P.A, c->wa);
     unsigned n = clampn(c->nN, P.cap);
     int32_t t = c->t;
     for (int64_t base = gthread() - (threadIdx.x & 31); base < n; base += nthreads()) {
@@ -305,6 +334,17 @@ __global__ void k_adv_select(PeelView<CT> P) {
         }
     }
 }
+
+template <typename CT>
+__global__ void k_adv_min(PeelView<CT> P) { phase_adv_min(P); }
+template <typename CT>
+__global__ void k_refill_scan(PeelView<CT> P) { phase_refill_scan(P); }
+template <typename CT>
+__global__ void k_refill_hist(PeelView<CT> P) { phase_refill_hist(P); }
+template <typename CT>
+__global__ void k_refill_select(PeelView<CT> P) { phase_refill_select(P); }
+template <typename CT>
+__global__ void k_adv_select(PeelView<CT> P) { phase_adv_select(P); }
 
 // ------------------------------------------------------------------------------------
 // Update
@@ -330,10 +370,10 @@ __device__ __forceinline__ RoundEnv<CT> round_env(const PeelView<CT>& P) {
     E.t = c->t;
     E.k = adv ? knew_of(c) : c->k;
     E.hi = c->hi;
-    E.A = P.A[c->wa];
+    E.A = pick(P.A, c->wa);
     E.nA = clampn(adv ? c->cntA : c->nA, P.cap);
-    E.next = P.A[c->wa ^ 1];
-    E.Ncur = adv ? P.N[c->wn ^ 1] : P.N[c->wn];
+    E.next = pick(P.A, c->wa ^ 1);
+    E.Ncur = adv ? pick(P.N, c->wn ^ 1) : pick(P.N, c->wn);
     E.ncnt = adv ? &c->nN2 : &c->nN;
     return E;
 }
@@ -349,21 +389,23 @@ __device__ __forceinline__ void dec_one(const RoundEnv<CT>& E, int32_t x) {
     if (o >= E.hi && o - 1 < E.hi) nd_append(E.ncnt, E.Ncur, E.P.cap, x, &E.P.ctl->err);
 }
 
-// Update-Func for the s-clique S made of R and the other r-subsets o[0..M).
+// Update-Func for the s-clique S made of R and the other r-subsets o[0..M). Returns whether S
+// was live (no r-subset peeled in an earlier round).
 template <typename CT, int M>
-__device__ __forceinline__ void update_func(const RoundEnv<CT>& E, int32_t R, const int32_t (&o)[M]) {
+__device__ __forceinline__ bool update_func(const RoundEnv<CT>& E, int32_t R, const int32_t (&o)[M]) {
     int32_t ro[M];
     int32_t owner = R;
 #pragma unroll
     for (int i = 0; i < M; ++i) {
         ro[i] = E.P.rnd[o[i]];
-        if (ro[i] < E.t) return;  // an r-subset was peeled in an earlier round
+        if (ro[i] < E.t) return false;  // an r-subset was peeled in an earlier round
         if (ro[i] == E.t && o[i] < owner) owner = o[i];
     }
-    if (owner != R) return;
+    if (owner != R) return true;
 #pragma unroll
     for (int i = 0; i < M; ++i)
         if (ro[i] != E.t) dec_one(E, o[i]);
+    return true;
 }
 
 __device__ __forceinline__ void add_listed(PeelCtl* c, unsigned long long v) {
@@ -371,91 +413,87 @@ __device__ __forceinline__ void add_listed(PeelCtl* c, unsigned long long v) {
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(&c->listed, v);
 }
 
+// Each Update variant is a functor with
+//   work(g, R):                 length of the list that drives R's listing;
+//   run(g, E, R, j0, dj, lst):  lists the s-cliques containing R from driver entries
+//                               j0, j0 + dj, ... (lanes of one warp: j0 = lane, dj = 32;
+//                               the whole grid on one heavy R: j0 = global lane, dj = all lanes).
+// The light kernel gives each warp one R at a time and defers R with work > kHeavy to a list that
+// the heavy kernel then spreads over every warp of the grid, so a few hub r-cliques in a round do
+// not serialise on single warps.
+constexpr int64_t kHeavy = 4096;
+
 // (1,2): R = v; S = {v, w} for every neighbour w.
 template <typename CT>
-__global__ void k_update12(GraphView g, PeelView<CT> P) {
-    if (P.ctl->done) return;
-    RoundEnv<CT> E = round_env(P);
-    int lane = threadIdx.x & 31;
-    unsigned long long listed = 0;
-    for (int64_t i = gwarp(); i < E.nA; i += nwarps()) {
-        int32_t v = E.A[i];
+struct Upd12 {
+    __device__ static int64_t work(const GraphView& g, int32_t v) { return g.rp[v + 1] - g.rp[v]; }
+    __device__ static void run(const GraphView& g, const RoundEnv<CT>& E, int32_t v, int64_t j0, int64_t dj,
+                               unsigned long long& listed) {
         int64_t b = g.rp[v], e = g.rp[v + 1];
-        for (int64_t p = b + lane; p < e; p += 32) {
+        for (int64_t p = b + j0; p < e; p += dj) {
             int32_t o[1] = {g.col[p]};
-            listed++;
-            update_func<CT, 1>(E, v, o);
+            listed += update_func<CT, 1>(E, v, o) ? 1 : 0;
         }
     }
-    add_listed(P.ctl, listed);
-}
+};
 
 // (1,3): R = v; S = {v, w, x} for every edge w -> x of DG inside N(v).
 template <typename CT>
-__global__ void k_update13(GraphView g, PeelView<CT> P) {
-    if (P.ctl->done) return;
-    RoundEnv<CT> E = round_env(P);
-    int lane = threadIdx.x & 31;
-    unsigned long long listed = 0;
-    for (int64_t i = gwarp(); i < E.nA; i += nwarps()) {
-        int32_t v = E.A[i];
+struct Upd13 {
+    __device__ static int64_t work(const GraphView& g, int32_t v) { return g.rp[v + 1] - g.rp[v]; }
+    __device__ static void run(const GraphView& g, const RoundEnv<CT>& E, int32_t v, int64_t j0, int64_t dj,
+                               unsigned long long& listed) {
         int64_t b = g.rp[v], e = g.rp[v + 1];
-        for (int64_t p = b + lane; p < e; p += 32) {
+        for (int64_t p = b + j0; p < e; p += dj) {
             int32_t w = g.col[p];
             for (int64_t jx = g.dg_rp[w]; jx < g.dg_rp[w + 1]; ++jx) {
                 int32_t x = g.dg_col[jx];
                 if (nd_find(g.col + b, e - b, x) < 0) continue;
                 int32_t o[2] = {w, x};
-                listed++;
-                update_func<CT, 2>(E, v, o);
+                listed += update_func<CT, 2>(E, v, o) ? 1 : 0;
             }
         }
     }
-    add_listed(P.ctl, listed);
-}
+};
 
 // (2,3): R = (u,v); S = {u, v, w} for w in N(u) ∩ N(v).
 template <typename CT>
-__global__ void k_update23(GraphView g, PeelView<CT> P) {
-    if (P.ctl->done) return;
-    RoundEnv<CT> E = round_env(P);
-    int lane = threadIdx.x & 31;
-    unsigned long long listed = 0;
-    for (int64_t i = gwarp(); i < E.nA; i += nwarps()) {
-        int32_t R = E.A[i];
+struct Upd23 {
+    __device__ static int64_t work(const GraphView& g, int32_t R) {
+        int32_t u = g.eu[R], v = g.ev[R];
+        int64_t du = g.rp[u + 1] - g.rp[u], dv = g.rp[v + 1] - g.rp[v];
+        return du < dv ? du : dv;
+    }
+    __device__ static void run(const GraphView& g, const RoundEnv<CT>& E, int32_t R, int64_t j0, int64_t dj,
+                               unsigned long long& listed) {
         int32_t u = g.eu[R], v = g.ev[R];
         int64_t xb = g.rp[u], xe = g.rp[u + 1], yb = g.rp[v], ye = g.rp[v + 1];
         if (xe - xb > ye - yb) {
             int64_t t0 = xb, t1 = xe;
             xb = yb, xe = ye, yb = t0, ye = t1;
         }
-        for (int64_t p = xb + lane; p < xe; p += 32) {
+        for (int64_t p = xb + j0; p < xe; p += dj) {
             int32_t w = g.col[p];
             int64_t q = nd_find(g.col + yb, ye - yb, w);
             if (q < 0) continue;
             int32_t o[2] = {g.pos2e[p], g.pos2e[yb + q]};
-            listed++;
-            update_func<CT, 2>(E, R, o);
+            listed += update_func<CT, 2>(E, R, o) ? 1 : 0;
         }
     }
-    add_listed(P.ctl, listed);
-}
+};
 
 // (2,4): R = (u,v); S = {u, v, w, x} for w in N(u) ∩ N(v) and x in N_DG(w) ∩ N(u) ∩ N(v).
 template <typename CT>
-__global__ void k_update24(GraphView g, PeelView<CT> P) {
-    if (P.ctl->done) return;
-    RoundEnv<CT> E = round_env(P);
-    int lane = threadIdx.x & 31;
-    unsigned long long listed = 0;
-    for (int64_t i = gwarp(); i < E.nA; i += nwarps()) {
-        int32_t R = E.A[i];
+struct Upd24 {
+    __device__ static int64_t work(const GraphView& g, int32_t R) { return Upd23<CT>::work(g, R); }
+    __device__ static void run(const GraphView& g, const RoundEnv<CT>& E, int32_t R, int64_t j0, int64_t dj,
+                               unsigned long long& listed) {
         int32_t u = g.eu[R], v = g.ev[R];
         int64_t ub = g.rp[u], un = g.rp[u + 1] - ub, vb = g.rp[v], vn = g.rp[v + 1] - vb;
         bool u_drives = un <= vn;
         int64_t xb = u_drives ? ub : vb, xn = u_drives ? un : vn;
         int64_t yb = u_drives ? vb : ub, yn = u_drives ? vn : un;
-        for (int64_t p = lane; p < xn; p += 32) {
+        for (int64_t p = j0; p < xn; p += dj) {
             int32_t w = g.col[xb + p];
             int64_t q = nd_find(g.col + yb, yn, w);
             if (q < 0) continue;
@@ -467,48 +505,250 @@ __global__ void k_update24(GraphView g, PeelView<CT> P) {
                 int64_t py = nd_find(g.col + yb, yn, x);
                 if (py < 0) continue;
                 int32_t o[5] = {e_xw, e_yw, g.pos2e[xb + px], g.pos2e[yb + py], g.dg_eid[jx]};
-                listed++;
-                update_func<CT, 5>(E, R, o);
+                listed += update_func<CT, 5>(E, R, o) ? 1 : 0;
             }
         }
     }
-    add_listed(P.ctl, listed);
-}
+};
 
 // (3,4): R = triangle (a,b,c) with edges ab, ac, bc; S = R + w for w in L(ab) ∩ L(ac) ∩ L(bc);
-// the three other triangles of S are read from the same table entries.
+// the three other triangles of S are the table entries of w in the three lists. The entries
+// carry the flags set by k_flag34: a DEAD entry's triangle was peeled in an earlier round, so
+// every S through it is dead and the candidate is dropped before any search; INA marks the
+// members of A for the owner rule. No per-triangle state is read at random.
+__device__ __forceinline__ void lists34(const GraphView& g, int32_t R, int64_t (&b)[3], int64_t (&n)[3]) {
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+        int32_t e = g.tri_e[3 * (int64_t)R + x];
+        b[x] = g.et_rp[e];
+        n[x] = g.et_rp[e + 1] - b[x];
+    }
+    // sort the three lists by length
+    if (n[1] < n[0]) {
+        int64_t tb = b[0], tn = n[0];
+        b[0] = b[1], n[0] = n[1], b[1] = tb, n[1] = tn;
+    }
+    if (n[2] < n[0]) {
+        int64_t tb = b[0], tn = n[0];
+        b[0] = b[2], n[0] = n[2], b[2] = tb, n[2] = tn;
+    }
+    if (n[2] < n[1]) {
+        int64_t tb = b[1], tn = n[1];
+        b[1] = b[2], n[1] = n[2], b[2] = tb, n[2] = tn;
+    }
+}
+
 template <typename CT>
-__global__ void k_update34(GraphView g, PeelView<CT> P) {
+struct Upd34 {
+    __device__ static int64_t work(const GraphView& g, int32_t R) {
+        int64_t b[3], n[3];
+        lists34(g, R, b, n);
+        return n[0];
+    }
+    __device__ static void run(const GraphView& g, const RoundEnv<CT>& E, int32_t R, int64_t j0, int64_t dj,
+                               unsigned long long& listed) {
+        const uint32_t* et = reinterpret_cast<const uint32_t*>(g.et_flags);
+        int64_t b[3], n[3];
+        lists34(g, R, b, n);
+        for (int64_t j = j0; j < n[0]; j += dj) {
+            uint32_t f0 = et[b[0] + j];
+            if (f0 & ND_ET_DEAD) continue;
+            int32_t w = g.et_w[b[0] + j];
+            int64_t q1 = nd_find(g.et_w + b[1], n[1], w);
+            if (q1 < 0) continue;
+            uint32_t f1 = et[b[1] + q1];
+            if (f1 & ND_ET_DEAD) continue;
+            int64_t q2 = nd_find(g.et_w + b[2], n[2], w);
+            if (q2 < 0) continue;
+            uint32_t f2 = et[b[2] + q2];
+            if (f2 & ND_ET_DEAD) continue;
+            listed++;
+            int32_t owner = R;
+            uint32_t fs[3] = {f0, f1, f2};
+#pragma unroll
+            for (int x = 0; x < 3; ++x)
+                if ((fs[x] & ND_ET_INA) && (int32_t)(fs[x] & ND_ET_ID) < owner) owner = (int32_t)(fs[x] & ND_ET_ID);
+            if (owner != R) continue;
+#pragma unroll
+            for (int x = 0; x < 3; ++x)
+                if (!(fs[x] & ND_ET_INA)) dec_one(E, (int32_t)(fs[x] & ND_ET_ID));
+        }
+    }
+};
+
+template <typename CT, typename U>
+__device__ void phase_update(const GraphView& g, const PeelView<CT>& P) {
     if (P.ctl->done) return;
     RoundEnv<CT> E = round_env(P);
     int lane = threadIdx.x & 31;
     unsigned long long listed = 0;
     for (int64_t i = gwarp(); i < E.nA; i += nwarps()) {
         int32_t R = E.A[i];
-        int32_t e0 = g.tri_e[3 * (int64_t)R], e1 = g.tri_e[3 * (int64_t)R + 1], e2 = g.tri_e[3 * (int64_t)R + 2];
-        int64_t b0 = g.et_rp[e0], n0 = g.et_rp[e0 + 1] - b0;
-        int64_t b1 = g.et_rp[e1], n1 = g.et_rp[e1 + 1] - b1;
-        int64_t b2 = g.et_rp[e2], n2 = g.et_rp[e2 + 1] - b2;
-        if (n1 < n0) {
-            int64_t tb = b0, tn = n0;
-            b0 = b1, n0 = n1, b1 = tb, n1 = tn;
+        if (U::work(g, R) > kHeavy) {
+            int queued = 0;
+            if (lane == 0) {
+                unsigned slot = atomicAdd(&P.ctl->nH, 1u);
+                if (slot < P.hcap) {
+                    P.H[slot] = R;
+                    queued = 1;
+                }
+            }
+            if (__shfl_sync(0xffffffffu, queued, 0)) continue;
         }
-        if (n2 < n0) {
-            int64_t tb = b0, tn = n0;
-            b0 = b2, n0 = n2, b2 = tb, n2 = tn;
-        }
-        for (int64_t j = lane; j < n0; j += 32) {
-            int32_t w = g.et_w[b0 + j];
-            int64_t q1 = nd_find(g.et_w + b1, n1, w);
-            if (q1 < 0) continue;
-            int64_t q2 = nd_find(g.et_w + b2, n2, w);
-            if (q2 < 0) continue;
-            int32_t o[3] = {g.et_t[b0 + j], g.et_t[b1 + q1], g.et_t[b2 + q2]};
-            listed++;
-            update_func<CT, 3>(E, R, o);
-        }
+        U::run(g, E, R, lane, 32, listed);
     }
     add_listed(P.ctl, listed);
+}
+
+template <typename CT, typename U>
+__device__ void phase_update_heavy(const GraphView& g, const PeelView<CT>& P) {
+    if (P.ctl->done) return;
+    unsigned nH = clampn(P.ctl->nH, P.hcap);
+    if (nH == 0) return;
+    RoundEnv<CT> E = round_env(P);
+    unsigned long long listed = 0;
+    int64_t j0 = gthread(), dj = nthreads();
+    for (unsigned h = 0; h < nH; ++h) U::run(g, E, P.H[h], j0, dj, listed);
+    add_listed(P.ctl, listed);
+}
+
+// Sets (kill = false) the INA flag, or replaces it by DEAD (kill = true), on the three table
+// entries of every triangle of this round's A.
+template <typename CT, bool kKill>
+__device__ void phase_flag34(const GraphView& g, const PeelView<CT>& P) {
+    PeelCtl* c = P.ctl;
+    if (c->done) return;
+    bool adv = c->mode & ND_MODE_ADV;
+    unsigned nA = clampn(adv ? c->cntA : c->nA, P.cap);
+    const int32_t* A = pick(P.A, c->wa);
+    for (int64_t i = gthread(); i < 3 * (int64_t)nA; i += nthreads()) {
+        int64_t R = A[i / 3];
+        int slot = (int)(i % 3);
+        int32_t e = g.tri_e[3 * R + slot];
+        int64_t pos = g.et_rp[e] + g.tri_pos[3 * R + slot];
+        uint32_t v = (uint32_t)g.et_flags[pos];
+        g.et_flags[pos] = (int32_t)(kKill ? ((v & ND_ET_ID) | ND_ET_DEAD) : (v | ND_ET_INA));
+    }
+}
+
+template <typename CT, typename U>
+__global__ void k_update(GraphView g, PeelView<CT> P) { phase_update<CT, U>(g, P); }
+template <typename CT, typename U>
+__global__ void k_update_heavy(GraphView g, PeelView<CT> P) { phase_update_heavy<CT, U>(g, P); }
+template <typename CT, bool kKill>
+__global__ void k_flag34(GraphView g, PeelView<CT> P) { phase_flag34<CT, kKill>(g, P); }
+
+// ------------------------------------------------------------------------------------
+// The whole peeling loop in one cooperative launch (every block resident at once), with a grid
+// barrier between phases. The barrier's arrive is a release and its poll an acquire at GPU
+// scope, so every write before the barrier is visible to every load after it. Its wait is
+// bounded by the global timer: after kBarrierTimeoutNs, or once another block has given up, a
+// block sets ctl->err bit 8 and returns, so an inconsistent state ends the kernel instead of
+// hanging it.
+constexpr unsigned long long kBarrierTimeoutNs = 60ull * 1000 * 1000 * 1000;
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_acquire_i32(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void red_release_add_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Returns false if the barrier gave up (timeout or another block's failure).
+__device__ bool grid_barrier(PeelCtl* c, unsigned long long& target) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        target += gridDim.x;
+        red_release_add_u64(&c->bar_arrive, 1ull);
+        unsigned long long t0 = globaltimer();
+        unsigned ns = 32;
+        int good = 1;
+        while (ld_acquire_u64(&c->bar_arrive) < target) {
+            if ((ld_acquire_i32(&c->err) & 8) || globaltimer() - t0 > kBarrierTimeoutNs) {
+                atomicOr(&c->err, 8);
+                good = 0;
+                break;
+            }
+            __nanosleep(ns);
+            if (ns < 1024) ns <<= 1;
+        }
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+template <typename CT, typename U, bool k34>
+__global__ void __launch_bounds__(256) k_peel_loop(GraphView g, PeelView<CT> P) {
+    PeelCtl* c = P.ctl;
+    unsigned long long target = 0;
+    for (;;) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) ctl_step(c, P.round_size, P.round_level, P.round_cap);
+        if (!grid_barrier(c, target)) return;
+        if (c->done) return;  // every block reads the same value after the barrier
+        if (c->mode & ND_MODE_ADV) {
+            phase_adv_min(P);
+            if (!grid_barrier(c, target)) return;
+            if (need_refill(c)) {
+                phase_refill_scan(P);
+                if (!grid_barrier(c, target)) return;
+                phase_refill_hist(P);
+                if (!grid_barrier(c, target)) return;
+                if (blockIdx.x == 0) phase_refill_pick(c);
+                if (!grid_barrier(c, target)) return;
+                phase_refill_select(P);
+                if (!grid_barrier(c, target)) return;
+            }
+            phase_adv_select(P);
+            if (!grid_barrier(c, target)) return;
+        }
+        if (k34) {
+            phase_flag34<CT, false>(g, P);
+            if (!grid_barrier(c, target)) return;
+        }
+        phase_update<CT, U>(g, P);
+        if (!grid_barrier(c, target)) return;
+        if (c->nH) {
+            phase_update_heavy<CT, U>(g, P);
+            if (!grid_barrier(c, target)) return;
+        }
+        if (k34) {
+            phase_flag34<CT, true>(g, P);
+            if (!grid_barrier(c, target)) return;
+        }
+    }
+}
+
+template <typename CT, typename U, bool k34>
+cudaError_t launch_peel_loop(const GraphView& g, const PeelView<CT>& P, cudaStream_t st) {
+    auto kern = k_peel_loop<CT, U, k34>;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+    int blocks = nd_sm_count() * (per_sm < 4 ? per_sm : 4);
+    GraphView gv = g;
+    PeelView<CT> pv = P;
+    void* args[] = {&gv, &pv};
+    e = cudaLaunchCooperativeKernel((const void*)kern, dim3(blocks), dim3(256), args, 0, st);
+    if (e == cudaSuccess) nd_note_launches(1);
+    return e;
 }
 
 int peel_blocks() { return nd_sm_count() * 4; }
@@ -520,26 +760,175 @@ void nd_peel_init(PeelCtl* ctl, int64_t n_r, int64_t max_rounds, cudaStream_t st
 }
 
 template <typename CT>
-void nd_peel_round(const GraphView& g, int r, int s, const PeelView<CT>& P, cudaStream_t st) {
+void nd_peel_ctl(const PeelView<CT>& P, cudaStream_t st, int use_cond, cudaGraphConditionalHandle h_loop,
+                 cudaGraphConditionalHandle h_adv) {
+    ND_K(k_ctl<<<1, 32, 0, st>>>(P.ctl, P.round_size, P.round_level, P.round_cap, use_cond, h_loop, h_adv));
+}
+
+template <typename CT>
+void nd_peel_adv_min(const PeelView<CT>& P, cudaStream_t st) {
+    ND_K(k_adv_min<CT><<<peel_blocks(), kThreads, 0, st>>>(P));
+}
+
+void nd_peel_set_refill(PeelCtl* ctl, cudaStream_t st, cudaGraphConditionalHandle h_refill) {
+    ND_K(k_set_refill<<<1, 32, 0, st>>>(ctl, h_refill));
+}
+
+template <typename CT>
+void nd_peel_refill(const PeelView<CT>& P, cudaStream_t st) {
     int nb = peel_blocks();
-    ND_K(k_ctl<<<1, 32, 0, st>>>(P.ctl, P.round_size, P.round_level, P.round_cap));
-    ND_K(k_adv_min<CT><<<nb, kThreads, 0, st>>>(P));
     ND_K(k_refill_scan<CT><<<nb, kThreads, 0, st>>>(P));
     ND_K(k_refill_hist<CT><<<nb, kThreads, 0, st>>>(P));
     ND_K(k_refill_pick<<<1, 1024, 0, st>>>(P.ctl));
     ND_K(k_refill_select<CT><<<nb, kThreads, 0, st>>>(P));
-    ND_K(k_adv_select<CT><<<nb, kThreads, 0, st>>>(P));
-    if (r == 1 && s == 2)
-        ND_K(k_update12<CT><<<nb, kThreads, 0, st>>>(g, P));
-    else if (r == 1 && s == 3)
-        ND_K(k_update13<CT><<<nb, kThreads, 0, st>>>(g, P));
-    else if (r == 2 && s == 3)
-        ND_K(k_update23<CT><<<nb, kThreads, 0, st>>>(g, P));
-    else if (r == 2 && s == 4)
-        ND_K(k_update24<CT><<<nb, kThreads, 0, st>>>(g, P));
-    else if (r == 3 && s == 4)
-        ND_K(k_update34<CT><<<nb, kThreads, 0, st>>>(g, P));
 }
+
+template <typename CT>
+void nd_peel_adv_select(const PeelView<CT>& P, cudaStream_t st) {
+    ND_K(k_adv_select<CT><<<peel_blocks(), kThreads, 0, st>>>(P));
+}
+
+template <typename CT>
+void nd_peel_update(const GraphView& g, int r, int s, const PeelView<CT>& P, cudaStream_t st) {
+    int nb = peel_blocks();
+    if (r == 1 && s == 2) {
+        ND_K(k_update<CT, Upd12<CT>><<<nb, kThreads, 0, st>>>(g, P));
+        ND_K(k_update_heavy<CT, Upd12<CT>><<<nb, kThreads, 0, st>>>(g, P));
+    } else if (r == 1 && s == 3) {
+        ND_K(k_update<CT, Upd13<CT>><<<nb, kThreads, 0, st>>>(g, P));
+        ND_K(k_update_heavy<CT, Upd13<CT>><<<nb, kThreads, 0, st>>>(g, P));
+    } else if (r == 2 && s == 3) {
+        ND_K(k_update<CT, Upd23<CT>><<<nb, kThreads, 0, st>>>(g, P));
+        ND_K(k_update_heavy<CT, Upd23<CT>><<<nb, kThreads, 0, st>>>(g, P));
+    } else if (r == 2 && s == 4) {
+        ND_K(k_update<CT, Upd24<CT>><<<nb, kThreads, 0, st>>>(g, P));
+        ND_K(k_update_heavy<CT, Upd24<CT>><<<nb, kThreads, 0, st>>>(g, P));
+    } else if (r == 3 && s == 4) {
+        ND_K(k_flag34<CT, false><<<nb, kThreads, 0, st>>>(g, P));
+        ND_K(k_update<CT, Upd34<CT>><<<nb, kThreads, 0, st>>>(g, P));
+        ND_K(k_update_heavy<CT, Upd34<CT>><<<nb, kThreads, 0, st>>>(g, P));
+        ND_K(k_flag34<CT, true><<<nb, kThreads, 0, st>>>(g, P));
+    }
+}
+
+// One round as a plain launch sequence (every phase launched; inactive ones return at once).
+template <typename CT>
+void nd_peel_round(const GraphView& g, int r, int s, const PeelView<CT>& P, cudaStream_t st) {
+    nd_peel_ctl<CT>(P, st, 0, 0, 0);
+    nd_peel_adv_min<CT>(P, st);
+    nd_peel_refill<CT>(P, st);
+    nd_peel_adv_select<CT>(P, st);
+    nd_peel_update<CT>(g, r, s, P, st);
+}
+
+// Adds a conditional node of the given type after the current capture point of st and returns
+// its body graph; the capture continues after the node.
+static cudaError_t capture_conditional(cudaStream_t st, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                                       cudaGraph_t* body) {
+    cudaStreamCaptureStatus status;
+    cudaGraph_t graph = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(st, &status, nullptr, &graph, &deps, nullptr, &ndeps);
+    if (e != cudaSuccess) return e;
+    if (status != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = type;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, graph, deps, nullptr, ndeps, &p);
+    if (e != cudaSuccess) return e;
+    *body = p.conditional.phGraph_out[0];
+    return cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
+// The whole peeling loop as one CUDA graph:
+//   WHILE (not done) { k_ctl; IF (advance) { k_adv_min; k_set_refill; IF (refill) { refill x4 };
+//                      k_adv_select }; Update kernels }
+// st, st2, st3 are three distinct streams used only for capture. On failure nothing is left
+// capturing and *out is NULL.
+template <typename CT>
+cudaError_t nd_peel_loop_graph(const GraphView& g, int r, int s, const PeelView<CT>& P, cudaStream_t st,
+                               cudaStream_t st2, cudaStream_t st3, cudaGraph_t* out) {
+    *out = nullptr;
+    cudaGraph_t graph = nullptr, body = nullptr, adv_body = nullptr, ref_body = nullptr, tmp = nullptr;
+    cudaGraphConditionalHandle h_loop, h_adv, h_refill;
+    cudaError_t e = cudaGraphCreate(&graph, 0);
+    if (e != cudaSuccess) return e;
+    auto fail = [&](cudaError_t err) {
+        cudaStreamCaptureStatus cs;
+        for (cudaStream_t x : {st3, st2, st}) {
+            if (cudaStreamIsCapturing(x, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+                cudaGraph_t junk = nullptr;
+                cudaStreamEndCapture(x, &junk);
+            }
+        }
+        nd_set_capturing(false);
+        cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return err;
+    };
+    if ((e = cudaGraphConditionalHandleCreate(&h_loop, graph, 1, cudaGraphCondAssignDefault)) != cudaSuccess ||
+        (e = cudaGraphConditionalHandleCreate(&h_adv, graph, 0, cudaGraphCondAssignDefault)) != cudaSuccess ||
+        (e = cudaGraphConditionalHandleCreate(&h_refill, graph, 0, cudaGraphCondAssignDefault)) != cudaSuccess)
+        return fail(e);
+    cudaGraphNodeParams wp = {};
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = h_loop;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    if ((e = cudaGraphAddNode(&wnode, graph, nullptr, nullptr, 0, &wp)) != cudaSuccess) return fail(e);
+    body = wp.conditional.phGraph_out[0];
+    nd_set_capturing(true);
+    if ((e = cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+        cudaSuccess)
+        return fail(e);
+    nd_peel_ctl<CT>(P, st, 1, h_loop, h_adv);
+    if ((e = capture_conditional(st, h_adv, cudaGraphCondTypeIf, &adv_body)) != cudaSuccess) return fail(e);
+    if ((e = cudaStreamBeginCaptureToGraph(st2, adv_body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+        cudaSuccess)
+        return fail(e);
+    nd_peel_adv_min<CT>(P, st2);
+    nd_peel_set_refill(P.ctl, st2, h_refill);
+    if ((e = capture_conditional(st2, h_refill, cudaGraphCondTypeIf, &ref_body)) != cudaSuccess) return fail(e);
+    if ((e = cudaStreamBeginCaptureToGraph(st3, ref_body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+        cudaSuccess)
+        return fail(e);
+    nd_peel_refill<CT>(P, st3);
+    if ((e = cudaStreamEndCapture(st3, &tmp)) != cudaSuccess) return fail(e);
+    nd_peel_adv_select<CT>(P, st2);
+    if ((e = cudaStreamEndCapture(st2, &tmp)) != cudaSuccess) return fail(e);
+    nd_peel_update<CT>(g, r, s, P, st);
+    if ((e = cudaStreamEndCapture(st, &tmp)) != cudaSuccess) return fail(e);
+    nd_set_capturing(false);
+    *out = graph;
+    return cudaSuccess;
+}
+
+// The whole loop as one cooperative kernel (see k_peel_loop). Fails without side effects if a
+// cooperative launch is not possible.
+template <typename CT>
+cudaError_t nd_peel_persistent(const GraphView& g, int r, int s, const PeelView<CT>& P, cudaStream_t st) {
+    if (r == 1 && s == 2) return launch_peel_loop<CT, Upd12<CT>, false>(g, P, st);
+    if (r == 1 && s == 3) return launch_peel_loop<CT, Upd13<CT>, false>(g, P, st);
+    if (r == 2 && s == 3) return launch_peel_loop<CT, Upd23<CT>, false>(g, P, st);
+    if (r == 2 && s == 4) return launch_peel_loop<CT, Upd24<CT>, false>(g, P, st);
+    if (r == 3 && s == 4) return launch_peel_loop<CT, Upd34<CT>, true>(g, P, st);
+    return cudaErrorInvalidValue;
+}
+
+// kernels launched per round by the loop graph (for the launch counter): the nodes executed in
+// a same-level round and the extra ones of an advance round
+int nd_peel_nodes_per_round(int r, int s) { return 1 + (r == 3 ? 4 : 2); }
 
 template void nd_peel_round<int32_t>(const GraphView&, int, int, const PeelView<int32_t>&, cudaStream_t);
 template void nd_peel_round<int64_t>(const GraphView&, int, int, const PeelView<int64_t>&, cudaStream_t);
+template cudaError_t nd_peel_persistent<int32_t>(const GraphView&, int, int, const PeelView<int32_t>&, cudaStream_t);
+template cudaError_t nd_peel_persistent<int64_t>(const GraphView&, int, int, const PeelView<int64_t>&, cudaStream_t);
+template cudaError_t nd_peel_loop_graph<int32_t>(const GraphView&, int, int, const PeelView<int32_t>&, cudaStream_t,
+                                                 cudaStream_t, cudaStream_t, cudaGraph_t*);
+template cudaError_t nd_peel_loop_graph<int64_t>(const GraphView&, int, int, const PeelView<int64_t>&, cudaStream_t,
+                                                 cudaStream_t, cudaStream_t, cudaGraph_t*);

@@ -1,0 +1,402 @@
+// Batches and serving: many independent graphs per device-resident run.
+//
+// A batch merges the requests that share an (r,s) into one disjoint union (vertex ids shifted
+// by the sizes of the graphs before it) and runs one decomposition on it. The (r,s) core number
+// of an r-clique depends only on its connected component, so each graph receives exactly the
+// numbers it gets alone; and because ids are shifted in request order, the union's canonical
+// r-clique order is the requests' canonical orders concatenated, so each request's result is
+// one contiguous slice. All graphs of a batch share the same peeling rounds, launches and CUDA
+// graphs instead of one launch sequence per graph.
+//
+// The server keeps a FIFO queue. Each of cfg.workers threads owns a stream (its own context on
+// the same device) and repeatedly forms a batch: the oldest waiting request plus later waiting
+// requests with the same (r,s), up to cfg.max_batch, admitted while the sum of their memory
+// estimates fits the budget next to the batches already running. Requests that arrive while
+// batches run are picked up by the next worker that frees up, so their work overlaps with the
+// batches already on the device (continuous batching at batch granularity).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "nd.h"
+#include "nd_common.cuh"
+#include "nd_host.h"
+
+namespace {
+
+bool rs_ok(int r, int s) {
+    return (r == 1 && (s == 2 || s == 3)) || (r == 2 && (s == 3 || s == 4)) || (r == 3 && s == 4);
+}
+
+__global__ void k_gather_offsets(const int64_t* __restrict__ ebase, const int64_t* __restrict__ tbase,
+                                 const int64_t* __restrict__ voff, int64_t count, int r, int64_t* __restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= count; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t v = voff[i];
+        int64_t o = v;
+        if (r >= 2) o = ebase[v];
+        if (r >= 3) o = tbase[o];
+        out[i] = o;
+    }
+}
+
+double now_ms() {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+int check_request(const nd_request& q) {
+    if (q.n < 0 || !q.rowptr || !rs_ok(q.r, q.s)) return ND_EINVAL;
+    if (q.rowptr[0] != 0 || q.rowptr[q.n] < 0 || (q.rowptr[q.n] > 0 && !q.col)) return ND_EINVAL;
+    return ND_OK;
+}
+
+// Runs one union decomposition for the requests in idx (all with the same (r,s)).
+int run_group(nd_ctx* ctx, nd_request* const* reqs, const std::vector<int>& idx, nd_batch_stats* st) {
+    int r = reqs[idx[0]]->r, s = reqs[idx[0]]->s;
+    int64_t total_n = 0, total_nnz = 0;
+    for (int i : idx) {
+        total_n += reqs[i]->n;
+        total_nnz += reqs[i]->rowptr[reqs[i]->n];
+    }
+    if (total_n > INT32_MAX) return nd_set_error(ND_EOVERFLOW, "batch: more than 2^31-1 vertices in one (r,s) group");
+    std::vector<int64_t> rp((size_t)total_n + 1);
+    std::vector<int32_t> col((size_t)std::max<int64_t>(total_nnz, 1));
+    std::vector<int64_t> voff(idx.size() + 1);
+    int64_t vo = 0, eo = 0;
+    for (size_t k = 0; k < idx.size(); ++k) {
+        const nd_request& q = *reqs[idx[k]];
+        voff[k] = vo;
+        for (int32_t v = 0; v < q.n; ++v) rp[vo + v] = eo + q.rowptr[v];
+        int64_t nnz = q.rowptr[q.n];
+        for (int64_t j = 0; j < nnz; ++j) col[eo + j] = q.col[j] + (int32_t)vo;
+        vo += q.n;
+        eo += nnz;
+    }
+    rp[total_n] = eo;
+    voff[idx.size()] = vo;
+    nd_graph* g = nullptr;
+    int rc = nd_load_csr(ctx, (int32_t)total_n, rp.data(), col.data(), 0, &g);
+    if (rc) return rc;
+    PeelOut po;
+    nd_stats S;
+    // the loop graph (not the cooperative kernel, which holds every SM) lets concurrent batches
+    // of the server overlap on the device
+    rc = nd_decompose_dev(g, r, s, 0, ND_PEEL_LOOP_GRAPH, po, &S);
+    std::vector<int64_t> off(idx.size() + 1);
+    if (!rc) {
+        DBuf dv, doff;
+        rc = nd_alloc(ctx, dv, sizeof(int64_t) * voff.size());
+        if (!rc) rc = nd_alloc(ctx, doff, sizeof(int64_t) * voff.size());
+        if (!rc) {
+            cudaMemcpyAsync(dv.p, voff.data(), sizeof(int64_t) * voff.size(), cudaMemcpyHostToDevice, ctx->stream);
+            GraphView v = nd_view(g);
+            ND_K(k_gather_offsets<<<std::max<int64_t>(1, ((int64_t)voff.size() + 255) / 256), 256, 0, ctx->stream>>>(
+                v.ebase, v.tbase, (const int64_t*)dv.p, (int64_t)idx.size(), r, (int64_t*)doff.p));
+            rc = nd_check_launch("batch offsets");
+            if (!rc) {
+                cudaMemcpyAsync(off.data(), doff.p, sizeof(int64_t) * off.size(), cudaMemcpyDeviceToHost,
+                                ctx->stream);
+                rc = nd_sync(ctx, "batch offsets");
+            }
+        }
+        nd_free(ctx, dv);
+        nd_free(ctx, doff);
+    }
+    if (!rc) {
+        std::vector<int32_t> core((size_t)std::max<int64_t>(S.n_r, 1));
+        if (S.n_r) {
+            cudaMemcpyAsync(core.data(), po.core.p, sizeof(int32_t) * S.n_r, cudaMemcpyDeviceToHost, ctx->stream);
+            rc = nd_sync(ctx, "batch results");
+        }
+        if (!rc) {
+            for (size_t k = 0; k < idx.size(); ++k) {
+                nd_request& q = *reqs[idx[k]];
+                int64_t a = off[k], b = off[k + 1];
+                q.n_r = b - a;
+                if (q.core_out) {
+                    if (q.core_cap < q.n_r) {
+                        q.status = ND_EINVAL;
+                        continue;
+                    }
+                    memcpy(q.core_out, core.data() + a, sizeof(int32_t) * (b - a));
+                }
+                q.status = ND_OK;
+            }
+            if (st) {
+                st->n_r_total += S.n_r;
+                st->n_s_total += S.n_s;
+                st->rho_max = std::max<int64_t>(st->rho_max, S.rho);
+            }
+        }
+    }
+    nd_free(ctx, po.core);
+    nd_free(ctx, po.rnd);
+    nd_graph_free(g);
+    return rc;
+}
+
+int batch_impl(nd_ctx* ctx, nd_request* const* reqs, int count, nd_batch_stats* st) {
+    double t0 = now_ms();
+    if (st) {
+        memset(st, 0, sizeof(*st));
+        st->requests = count;
+    }
+    std::vector<std::pair<int, int>> keys;
+    std::vector<std::vector<int>> groups;
+    int first_err = ND_OK;
+    for (int i = 0; i < count; ++i) {
+        nd_request& q = *reqs[i];
+        q.n_r = 0;
+        q.status = check_request(q);
+        if (q.status) {
+            if (!first_err) first_err = q.status;
+            continue;
+        }
+        std::pair<int, int> key(q.r, q.s);
+        size_t gi = std::find(keys.begin(), keys.end(), key) - keys.begin();
+        if (gi == keys.size()) {
+            keys.push_back(key);
+            groups.emplace_back();
+        }
+        groups[gi].push_back(i);
+    }
+    for (auto& grp : groups) {
+        int rc = run_group(ctx, reqs, grp, st);
+        if (rc) {
+            for (int i : grp) reqs[i]->status = rc;
+            if (!first_err) first_err = rc;
+        }
+        if (st) st->groups++;
+    }
+    for (int i = 0; i < count; ++i)
+        if (reqs[i]->status && !first_err) first_err = reqs[i]->status;
+    if (st) st->t_total_ms = now_ms() - t0;
+    if (first_err) return nd_set_error(first_err, "batch: %s", nd_last_error());
+    return ND_OK;
+}
+
+// A memory estimate for one request made before anything is counted: CSR, edge index and
+// orientation, plus per r-clique state; for r = 3 the triangle count is bounded by the wedge
+// count / 3 and by m sqrt(2m) / 3.
+size_t estimate_bytes(const nd_request& q) {
+    double n = q.n, m = (double)q.rowptr[q.n] / 2.0;
+    double bytes = 16 * (n + 1) + 8 * 2 * m + 16 * n + 4 * 2 * m + 8 * m + 8 * (n + 1) + 8 * m;
+    double nr = q.r == 1 ? n : m;
+    if (q.r == 3) {
+        double w = 0;
+        for (int32_t v = 0; v < q.n; ++v) {
+            double d = (double)(q.rowptr[v + 1] - q.rowptr[v]);
+            w += d * (d - 1) / 2;
+        }
+        nr = std::min(w / 3.0, m * std::sqrt(2.0 * m) / 3.0);
+        bytes += 16 * m + 48 * nr;  // per-edge table bounds + three entries per triangle
+    }
+    bytes += 40 * nr + 64 * 1024;  // counts, rounds, cores, work lists, control block
+    return (size_t)bytes;
+}
+
+}  // namespace
+
+extern "C" int nd_batch_run(nd_ctx* ctx, nd_request* reqs, int32_t count, nd_batch_stats* st) {
+    if (!ctx || (count > 0 && !reqs) || count < 0) return nd_set_error(ND_EINVAL, "nd_batch_run: bad arguments");
+    cudaSetDevice(ctx->device);
+    std::vector<nd_request*> ptrs(count);
+    for (int i = 0; i < count; ++i) ptrs[i] = &reqs[i];
+    return batch_impl(ctx, ptrs.data(), count, st);
+}
+
+// ------------------------------------------------------------------------------------
+// server
+
+struct Ticket {
+    nd_request req;
+    uint64_t id = 0;
+    int32_t status = ND_PENDING;
+    int32_t batch_size = 0;
+    double t_submit = 0, t_start = 0, t_done = 0;
+    size_t est = 0;
+};
+
+struct nd_server {
+    nd_ctx* ctx = nullptr;
+    nd_server_cfg cfg;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Ticket*> queue;
+    std::unordered_map<uint64_t, Ticket*> tickets;
+    uint64_t next_id = 1;
+    size_t used = 0;
+    int running = 0;
+    int64_t unfinished = 0;
+    bool stop = false;
+    std::vector<std::thread> threads;
+    std::vector<nd_ctx*> wctx;
+};
+
+static void worker_loop(nd_server* sv, int w) {
+    cudaSetDevice(sv->ctx->device);
+    nd_ctx* ctx = sv->wctx[w];
+    for (;;) {
+        std::vector<Ticket*> batch;
+        size_t est = 0;
+        {
+            std::unique_lock<std::mutex> lk(sv->mu);
+            sv->cv_work.wait(lk, [&] {
+                if (sv->stop && sv->queue.empty()) return true;
+                if (sv->queue.empty()) return false;
+                size_t need = sv->queue.front()->est;
+                return sv->cfg.mem_budget == 0 || sv->used + need <= sv->cfg.mem_budget || sv->running == 0;
+            });
+            if (sv->queue.empty()) return;  // stopping
+            Ticket* head = sv->queue.front();
+            int r = head->req.r, s = head->req.s;
+            for (auto it = sv->queue.begin(); it != sv->queue.end() && (int)batch.size() < sv->cfg.max_batch;) {
+                Ticket* t = *it;
+                bool fits = sv->cfg.mem_budget == 0 || sv->used + est + t->est <= sv->cfg.mem_budget ||
+                            (batch.empty() && sv->running == 0);
+                if (t->req.r == r && t->req.s == s && fits) {
+                    batch.push_back(t);
+                    est += t->est;
+                    it = sv->queue.erase(it);
+                } else if (t == head) {
+                    break;  // the oldest request does not fit yet
+                } else {
+                    ++it;
+                }
+            }
+            sv->used += est;
+            sv->running++;
+        }
+        double t0 = now_ms();
+        std::vector<nd_request*> reqs(batch.size());
+        for (size_t i = 0; i < batch.size(); ++i) reqs[i] = &batch[i]->req;
+        batch_impl(ctx, reqs.data(), (int)reqs.size(), nullptr);
+        double t1 = now_ms();
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            for (Ticket* t : batch) {
+                t->t_start = t0;
+                t->t_done = t1;
+                t->batch_size = (int32_t)batch.size();
+                t->status = t->req.status;
+                sv->unfinished--;
+            }
+            sv->used -= est;
+            sv->running--;
+        }
+        sv->cv_done.notify_all();
+        sv->cv_work.notify_all();
+    }
+}
+
+extern "C" int nd_server_create(nd_ctx* ctx, const nd_server_cfg* cfg, nd_server** out) {
+    if (!ctx || !cfg || !out) return nd_set_error(ND_EINVAL, "nd_server_create: NULL argument");
+    if (cfg->workers < 1 || cfg->max_batch < 1 || cfg->queue_cap < 1)
+        return nd_set_error(ND_EINVAL, "nd_server_create: workers, max_batch and queue_cap must be >= 1");
+    nd_server* sv = new nd_server();
+    sv->ctx = ctx;
+    sv->cfg = *cfg;
+    for (int w = 0; w < cfg->workers; ++w) {
+        nd_ctx* c = nullptr;
+        int rc = nd_ctx_create(ctx->device, nullptr, 0, &c);
+        if (rc) {
+            for (nd_ctx* x : sv->wctx) nd_ctx_destroy(x);
+            delete sv;
+            return rc;
+        }
+        nd_ctx_set_allocator(c, ctx->af, ctx->ff, ctx->user);
+        sv->wctx.push_back(c);
+    }
+    for (int w = 0; w < cfg->workers; ++w) sv->threads.emplace_back(worker_loop, sv, w);
+    *out = sv;
+    return ND_OK;
+}
+
+extern "C" int nd_submit(nd_server* sv, const nd_request* req, uint64_t* ticket) {
+    if (!sv || !req || !ticket) return nd_set_error(ND_EINVAL, "nd_submit: NULL argument");
+    if (check_request(*req)) return nd_set_error(ND_EINVAL, "nd_submit: malformed request");
+    Ticket* t = new Ticket();
+    t->req = *req;
+    t->req.status = ND_PENDING;
+    t->est = estimate_bytes(*req);
+    t->t_submit = now_ms();
+    if (sv->cfg.mem_budget && t->est > sv->cfg.mem_budget) {
+        size_t e = t->est;
+        delete t;
+        return nd_set_error(ND_ENOMEM, "nd_submit: request needs about %zu bytes, budget is %zu", e,
+                            sv->cfg.mem_budget);
+    }
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        if (sv->stop) {
+            delete t;
+            return nd_set_error(ND_EINVAL, "nd_submit: server is stopping");
+        }
+        if ((int)sv->queue.size() >= sv->cfg.queue_cap) {
+            delete t;
+            return nd_set_error(ND_EBUSY, "nd_submit: queue full (%d requests)", sv->cfg.queue_cap);
+        }
+        t->id = sv->next_id++;
+        sv->tickets[t->id] = t;
+        sv->queue.push_back(t);
+        sv->unfinished++;
+        *ticket = t->id;
+    }
+    sv->cv_work.notify_one();
+    return ND_OK;
+}
+
+extern "C" int nd_poll(nd_server* sv, uint64_t ticket, nd_result* res) {
+    if (!sv) return nd_set_error(ND_EINVAL, "nd_poll: NULL server");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->tickets.find(ticket);
+    if (it == sv->tickets.end()) return nd_set_error(ND_EINVAL, "nd_poll: unknown ticket %llu", (unsigned long long)ticket);
+    Ticket* t = it->second;
+    if (res) {
+        memset(res, 0, sizeof(*res));
+        res->status = t->status;
+        res->batch_size = t->batch_size;
+        res->n_r = t->req.n_r;
+        if (t->status != ND_PENDING) {
+            res->queue_ms = t->t_start - t->t_submit;
+            res->run_ms = t->t_done - t->t_start;
+            res->latency_ms = t->t_done - t->t_submit;
+        }
+    }
+    int st = t->status;
+    if (st != ND_PENDING) {
+        sv->tickets.erase(it);
+        delete t;
+    }
+    return st;
+}
+
+extern "C" int nd_server_drain(nd_server* sv) {
+    if (!sv) return nd_set_error(ND_EINVAL, "nd_server_drain: NULL server");
+    std::unique_lock<std::mutex> lk(sv->mu);
+    sv->cv_done.wait(lk, [&] { return sv->unfinished == 0; });
+    return ND_OK;
+}
+
+extern "C" int nd_server_destroy(nd_server* sv) {
+    if (!sv) return ND_OK;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stop = true;
+    }
+    sv->cv_work.notify_all();
+    for (auto& th : sv->threads) th.join();
+    for (nd_ctx* c : sv->wctx) nd_ctx_destroy(c);
+    for (auto& kv : sv->tickets) delete kv.second;
+    delete sv;
+    return ND_OK;
+}

@@ -63,7 +63,7 @@ def assert_parity(nd, ctx, g, r, s, **kw):
     assert np.array_equal(got["sizes"], want.sizes), tag
     assert np.array_equal(got["levels"], want.levels), tag
     assert got["st"]["n_s"] == wn_s and got["st"]["n_r"] == want.core.size, tag
-    assert got["st"]["listed"] == want.listed, tag
+    assert got["st"]["listed"] == want.live, tag
     if want.core.size:
         assert got["st"]["max_core"] == int(want.core.max()), tag
     return got
@@ -128,11 +128,21 @@ def test_count_width_and_launch_modes_agree(nd, ctx, r, s):
     g = gg.chung_lu(1500, 18.0, 2.1, seed=23)
     want = orc.decompose(g, r, s)
     for kw in [dict(count_width=4), dict(count_width=8), dict(flags=nd.ND_NO_GRAPH),
+               dict(flags=nd.ND_PEEL_LOOP_GRAPH), dict(flags=nd.ND_PEEL_PERSISTENT),
                dict(orient=nd.ND_ORIENT_DEGENERACY)]:
         got = run_gpu(nd, ctx, g, r, s, **kw)
         assert np.array_equal(got["core"], want.core), kw
         assert np.array_equal(got["round"], want.round), kw
         assert got["rho"] == want.rho, kw
+        assert got["st"]["listed"] == want.live, kw
+
+
+@pytest.mark.parametrize("mode", ["NO_GRAPH", "PEEL_LOOP_GRAPH", "PEEL_PERSISTENT"])
+def test_launch_modes_on_rmat(nd, ctx, mode):
+    """Every way of launching the peeling rounds gives the oracle's result, rounds included."""
+    g = gg.rmat(12, 16, 0.57, 0.19, 0.19, seed=6)
+    for r, s in [(2, 3), (3, 4), (1, 2)]:
+        assert_parity(nd, ctx, g, r, s, flags=getattr(nd, "ND_" + mode))
 
 
 def test_determinism(nd, ctx):
