@@ -323,9 +323,6 @@ def main():
     peel_ms = [sum(st[(r, s)]["t_peel_ms"] for r, s in wl["rs"]) for st in per_step_stats]
     peeled_per_s = rcl_per_step * args.steps * world / (sum(peel_ms) / 1000.0)
 
-    # roofline of the dominant kernel: the (r,s) = (3,4) counting kernel when present, else the
-    # (2,3) one; algorithmic bytes = the index entries every r-clique must read plus the matched
-    # list entries ("Roofline")
     roof = roofline(wl, per_step_stats, g)
 
     line = {"metric": "(r,s) s-cliques/sec", "value": value, "unit": "s-cliques/s", "n_gpus": world,
@@ -339,7 +336,7 @@ def main():
             "r_cliques_peeled_per_s": peeled_per_s,
             "wall_s_timed": wall,
             "per_rs": {f"({r},{s})": {k: stats[(r, s)][k] for k in
-                                      ("n_r", "n_s", "rho", "max_core", "listed", "advances", "refills",
+                                      ("n_r", "n_s", "rho", "max_core", "listed", "decrements", "advances", "refills",
                                        "count_width", "t_orient_ms", "t_index_ms", "t_count_ms", "t_peel_ms",
                                        "t_total_ms")} for r, s in wl["rs"]},
             "gpu_launches": launches,
@@ -367,6 +364,9 @@ def main():
 
 
 def roofline(wl, per_step_stats, g):
+    """HBM roofline of the dominant kernel (largest share of the step, from the library's CUDA
+    events on the launching stream), with the algorithmic-byte models stated in the design doc.
+    The other major kernels are reported beside it."""
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -376,29 +376,43 @@ def roofline(wl, per_step_stats, g):
     src = "measured"
     if not peak:
         peak, src = 6800.0, "fallback"
-    rs = (3, 4) if (3, 4) in wl["rs"] else wl["rs"][0]
-    r, s = rs
-    ts = [st[rs]["t_count_ms"] for st in per_step_stats]
-    st = per_step_stats[-1][rs]
-    n_r, n_s = st["n_r"], st["n_s"]
-    if rs == (3, 4):
-        # per triangle: 3 edge ids (12 B) + 3 list bounds (48 B) + the count (4 B); per (triangle,
-        # common neighbour) pair the entry in each of the three lists (12 B); sum of counts = 4 n_4
-        alg = 64 * n_r + 12 * 4 * n_s
-        kernel = "k_count34"
-    elif rs == (2, 3):
-        # per edge: endpoints (8 B) + 2 row bounds (32 B) + count (4 B); per (edge, common
-        # neighbour) the entry in both rows (8 B); sum of counts = 3 n_3
-        alg = 44 * n_r + 8 * 3 * n_s
-        kernel = "k_count23"
-    else:
-        alg = 0
-        kernel = "k_count%d%d" % rs
-    t = statistics.mean(ts) / 1000.0
-    achieved = alg / t / 1e9 if t > 0 else 0.0
-    return {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": None, "peak_source": src,
-            "algorithmic_bytes_per_launch": alg, "avg_launch_ms": t * 1000.0}
+    entries = []
+    for r, s in wl["rs"]:
+        st = per_step_stats[-1][(r, s)]
+        n_r, n_s = st["n_r"], st["n_s"]
+        destroyed, decs = st["listed"], st["decrements"]
+        t_count = statistics.mean(x[(r, s)]["t_count_ms"] for x in per_step_stats) / 1000.0
+        t_peel = statistics.mean(x[(r, s)]["t_peel_ms"] for x in per_step_stats) / 1000.0
+        if (r, s) == (3, 4):
+            # count: per triangle 3 edge ids (12 B) + 6 list bounds (48 B) + the count (4 B); per
+            # (triangle, common neighbour) the entry in the two lists intersected (8 B); sum = 4 n_4
+            count_b = 64 * n_r + 8 * 4 * n_s
+            # peel: per triangle edge ids, list bounds, entry offsets (72 B); per destroyed
+            # 4-clique its fourth vertex and the three sibling entries' tag and id (28 B); per
+            # decrement a count read + write (8 B)
+            peel_b = 72 * n_r + 28 * destroyed + 8 * decs
+        elif (r, s) == (2, 3):
+            # count: per edge endpoints (8 B) + 2 row bounds (32 B) + count (4 B); per (edge,
+            # common neighbour) the entry in both rows (8 B); sum = 3 n_3
+            count_b = 44 * n_r + 8 * 3 * n_s
+            # peel: per edge endpoints + row bounds (40 B); per destroyed triangle the two other
+            # edge ids and their rounds (16 B); per decrement read + write (8 B)
+            peel_b = 40 * n_r + 16 * destroyed + 8 * decs
+        else:
+            count_b = peel_b = 0
+        entries.append(("k_count%d%d" % (r, s), count_b, t_count))
+        entries.append(("k_peel_loop(%d,%d)" % (r, s), peel_b, t_peel))
+    entries.sort(key=lambda e: -e[2])
+
+    def one(name, b, t):
+        a = b / t / 1e9 if t > 0 else 0.0
+        return {"bound": "hbm", "kernel": name, "achieved": a, "peak": peak, "unit": "GB/s", "frac": a / peak,
+                "traffic": None, "peak_source": src + " (hbm_gbs)", "algorithmic_bytes_per_launch": b,
+                "avg_launch_ms": 1000.0 * t}
+
+    top = one(*entries[0])
+    top["others"] = [one(*e) for e in entries[1:]]
+    return top
 
 
 def e2e(nd, wl, g, local, width, steps, world, pg):

@@ -85,7 +85,8 @@ typedef struct nd_stats {
     int64_t rho;        /* peeling rounds: each round peels every unpeeled r-clique whose count
                            is <= k, after k = max(k, minimum unpeeled count) */
     int64_t max_core;   /* largest core number */
-    int64_t listed;     /* (s-clique, peeled member) pairs re-listed by Update over the run */
+    int64_t listed;     /* s-cliques destroyed by Update over the run (each exactly once, by the
+                           smallest member of A it contains): equals n_s */
     int64_t advances;   /* rounds that moved to a new level k */
     int64_t refills;    /* bucket-window rebuilds */
     int32_t count_width;/* 4 or 8: bytes per count used on the device */
@@ -95,6 +96,7 @@ typedef struct nd_stats {
     double t_count_ms;  /* s-clique counting */
     double t_peel_ms;   /* the peeling loop */
     double t_total_ms;
+    int64_t decrements; /* count decrements applied by Update over the run */
 } nd_stats;
 
 /* ---- context ------------------------------------------------------------------------- */

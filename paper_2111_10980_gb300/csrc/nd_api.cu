@@ -318,7 +318,6 @@ GraphView nd_view(const nd_graph* g) {
     v.tbase = (const int64_t*)g->tbase.p;
     v.tri_e = (const int32_t*)g->tri_e.p;
     v.tri_pos = (const int32_t*)g->tri_pos.p;
-    v.et_flags = (int32_t*)g->et_t.p;
     v.n3 = g->n3;
     return v;
 }
@@ -455,9 +454,7 @@ static int ensure_tri(nd_graph* g) {
     int64_t n3 = tot[1];
     if (tot[0] != 3 * n3) return nd_set_error(ND_EINTERNAL, "triangle index: %lld entries for %lld triangles",
                                               (long long)tot[0], (long long)n3);
-    // triangle ids share et_t with two flag bits (ND_ET_DEAD, ND_ET_INA)
-    if (n3 > (int64_t)ND_ET_ID)
-        return nd_set_error(ND_EOVERFLOW, "%lld triangles: more than 2^30-1", (long long)n3);
+    if (n3 > INT32_MAX) return nd_set_error(ND_EOVERFLOW, "%lld triangles: more than 2^31-1", (long long)n3);
     if ((rc = nd_alloc(c, g->et_w, sizeof(int32_t) * std::max<int64_t>(3 * n3, 1))) ||
         (rc = nd_alloc(c, g->et_t, sizeof(int32_t) * std::max<int64_t>(3 * n3, 1))) ||
         (rc = nd_alloc(c, g->tri_e, sizeof(int32_t) * std::max<int64_t>(3 * n3, 1))) ||
@@ -604,13 +601,13 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
     int64_t cap = std::max<int64_t>(n_r, 1);
     int64_t rcap = std::min<int64_t>(n_r, (int64_t)1 << 22) + 1;
     int64_t hcap = std::min<int64_t>(cap, (int64_t)1 << 20);
-    DBuf ctl, A0, A1, N0, N1, L0, L1, H, rs, rl;
+    DBuf ctl, A0, A1, N0, N1, L0, L1, H, rs, rl, etr;
     int rc = ND_OK;
     if ((rc = nd_alloc(c, ctl, sizeof(PeelCtl))) || (rc = nd_alloc(c, A0, 4 * cap)) || (rc = nd_alloc(c, A1, 4 * cap)) ||
         (rc = nd_alloc(c, N0, 4 * cap)) || (rc = nd_alloc(c, N1, 4 * cap)) || (rc = nd_alloc(c, L0, 4 * cap)) ||
         (rc = nd_alloc(c, L1, 4 * cap)) || (rc = nd_alloc(c, H, 4 * hcap)) || (rc = nd_alloc(c, rs, 8 * rcap)) ||
-        (rc = nd_alloc(c, rl, 8 * rcap))) {
-        for (DBuf* b : {&ctl, &A0, &A1, &N0, &N1, &L0, &L1, &H, &rs, &rl}) nd_free(c, *b);
+        (rc = nd_alloc(c, rl, 8 * rcap)) || (r == 3 && (rc = nd_alloc(c, etr, 4 * std::max<int64_t>(3 * g->n3, 1))))) {
+        for (DBuf* b : {&ctl, &A0, &A1, &N0, &N1, &L0, &L1, &H, &rs, &rl, &etr}) nd_free(c, *b);
         return rc;
     }
     PeelView<CT> P;
@@ -630,11 +627,21 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
     P.round_size = (int64_t*)rs.p;
     P.round_level = (int64_t*)rl.p;
     P.round_cap = rcap;
+    P.et_rnd = nullptr;
+    P.tri_e = nullptr;
+    P.tri_pos = nullptr;
+    P.et_rp = nullptr;
+    if (r == 3) {
+        P.et_rnd = (int32_t*)etr.p;
+        P.tri_e = (const int32_t*)g->tri_e.p;
+        P.tri_pos = (const int32_t*)g->tri_pos.p;
+        P.et_rp = (const int64_t*)g->et_rp.p;
+        nd_fill_i32(P.et_rnd, ND_UNPEELED, 3 * g->n3, st);
+    }
     nd_fill_i32(P.rnd, ND_UNPEELED, n_r, st);
     nd_fill_i32(P.core, 0, n_r, st);
     nd_peel_init(P.ctl, n_r, n_r + 2, st);
     GraphView v = nd_view(g);
-    if (r == 3) nd_edge_clear_flags(v, st);  // flags of a previous (3,4) peel on this graph
     bool looped = false;
     int persistent_launches = 0;
     bool want_persistent = (flags & ND_PEEL_PERSISTENT) || !(flags & (ND_NO_GRAPH | ND_PEEL_LOOP_GRAPH));
@@ -734,6 +741,7 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
                 nd_note_launches((int64_t)(h.t + 1) * nd_peel_nodes_per_round(r, s) + 3 * (int64_t)h.advances +
                                  4 * (int64_t)h.refills);
             po.listed = (int64_t)h.listed;
+            po.decs = (int64_t)h.decs;
             po.advances = h.advances;
             po.refills = h.refills;
             if (h.k > INT32_MAX && !rc) rc = nd_set_error(ND_EOVERFLOW, "a core number exceeds 2^31-1");
@@ -749,7 +757,7 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
             rc = nd_sync(c, "peel record");
         }
     }
-    for (DBuf* b : {&ctl, &A0, &A1, &N0, &N1, &L0, &L1, &H, &rs, &rl}) nd_free(c, *b);
+    for (DBuf* b : {&ctl, &A0, &A1, &N0, &N1, &L0, &L1, &H, &rs, &rl, &etr}) nd_free(c, *b);
     return rc;
 }
 
@@ -795,6 +803,7 @@ int nd_decompose_dev(nd_graph* g, int r, int s, int count_width, int flags, Peel
     S.rho = po.rho;
     S.max_core = po.max_core;
     S.listed = po.listed;
+    S.decrements = po.decs;
     S.advances = po.advances;
     S.refills = po.refills;
     S.count_width = w;

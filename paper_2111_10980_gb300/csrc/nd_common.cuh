@@ -14,17 +14,14 @@
 //                        tbase int64[m+1]  exclusive scan of |{w in L(a,b) : w > b}|
 //                        tri_e int32[3 n3] edges (ab, ac, bc) of triangle (a<b<c)
 //                        tri_pos int32[3 n3] offset of the triangle's entry in L(ab), L(ac), L(bc)
-//   During a (3,4) peel the two top bits of et_t flag the entry's triangle: ND_ET_DEAD (peeled
-//   in an earlier round) and ND_ET_INA (in the current round's A); ids therefore stay < 2^30.
+//   During a (3,4) peel, et_rnd int32[3 n3] (beside et_t) holds, per entry, the round in which
+//   the entry's triangle is peeled (INT32_MAX while unscheduled).
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #define ND_UNPEELED 0x7fffffff
-#define ND_ET_DEAD 0x80000000u
-#define ND_ET_INA 0x40000000u
-#define ND_ET_ID 0x3fffffffu
 #define ND_WARP 32
 
 // ------------------------------------------------------------------------------------
@@ -74,6 +71,52 @@ __device__ __forceinline__ int64_t nd_append(unsigned int* counter, int32_t* lis
     return slot;
 }
 
+// Windowed warp merge of two ascending lists (all 32 lanes call it with the same arguments).
+// Each step holds A[a .. a+32) and B[b .. b+32) in registers, lane i owning A[a+i] and B[b+i]
+// (INT32_MAX past the ends). Every lane finds the lower bound of its A element in the B window
+// with a 5-step search over shuffles; then the window with the smaller last element moves on
+// (both on a tie). Every element is loaded once, coalesced, and every common element is seen
+// exactly once, in the step whose windows hold both copies. visit(lane_active, ia, ib) is called
+// by every lane at every step; when lane_active is true, A[ia] == B[ib] is a common element.
+template <typename Visit>
+__device__ __forceinline__ void nd_warp_merge(const int32_t* __restrict__ A, int64_t na, const int32_t* __restrict__ B,
+                                              int64_t nb, Visit visit) {
+    const unsigned full = 0xffffffffu;
+    int lane = threadIdx.x & 31;
+    int64_t a = 0, b = 0;
+    int32_t av = lane < na ? __ldg(A + lane) : 0x7fffffff;
+    int32_t bv = lane < nb ? __ldg(B + lane) : 0x7fffffff;
+    while (a < na && b < nb) {
+        int la = (int)((na - a < 32 ? na - a : 32) - 1);
+        int lb = (int)((nb - b < 32 ? nb - b : 32) - 1);
+        int32_t amax = __shfl_sync(full, av, la);
+        int32_t bmax = __shfl_sync(full, bv, lb);
+        int lo = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            int32_t probe = __shfl_sync(full, bv, lo + step - 1);
+            if (probe < av) lo += step;
+        }
+        int32_t hit = __shfl_sync(full, bv, lo);
+        bool found = lane <= la && hit == av;
+        visit(found, a + lane, b + lo);
+        if (amax <= bmax) {
+            a += 32;
+            av = a + lane < na ? __ldg(A + a + lane) : 0x7fffffff;
+        }
+        if (bmax <= amax) {
+            b += 32;
+            bv = b + lane < nb ? __ldg(B + b + lane) : 0x7fffffff;
+        }
+    }
+}
+
+// Use the warp merge when the longer list is at most this many times the shorter one (plus a
+// constant), else per-lane binary searches of the shorter list's elements in the longer one.
+__device__ __forceinline__ bool nd_prefer_merge(int64_t n_short, int64_t n_long) {
+    return n_long <= 8 * n_short + 64;
+}
+
 __device__ __forceinline__ int64_t nd_atomic_dec(int32_t* p) { return (int64_t)atomicSub(p, 1); }
 __device__ __forceinline__ int64_t nd_atomic_dec(int64_t* p) {
     return (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(p), 0xffffffffffffffffull);
@@ -105,7 +148,6 @@ struct GraphView {
     const int64_t* tbase;
     const int32_t* tri_e;
     const int32_t* tri_pos;
-    int32_t* et_flags;  // et_t, writable view for the (3,4) peel's flag bits
     int64_t n3;
 };
 
@@ -141,10 +183,13 @@ struct PeelCtl {
     unsigned int nH;    // r-cliques of this round's A deferred to the heavy Update kernel
     unsigned long long minN;  // min count over unpeeled members of N (adv_min)
     unsigned long long gmin;  // min count over unpeeled r-cliques (refill)
-    // grid barrier of the persistent peel kernel (arrivals since the launch)
+    // grid barrier of the persistent peel kernel: arrivals since the launch, and the arrival
+    // count up to which blocks have been released
     unsigned long long bar_arrive;
+    unsigned long long bar_gen;
     // statistics
     unsigned long long listed;
+    unsigned long long decs;
     long long advances, refills;
     unsigned long long hist[ND_HBINS];
 };
@@ -159,6 +204,12 @@ struct PeelView {
     int32_t* L[2];
     int32_t* H;      // heavy r-cliques of the current round (capacity hcap)
     uint32_t hcap;
+    // (3,4) only: the round tag of every triangle-index entry, and what is needed to find the
+    // three entries of a triangle (NULL for other (r,s))
+    int32_t* et_rnd;
+    const int32_t* tri_e;
+    const int32_t* tri_pos;
+    const int64_t* et_rp;
     uint32_t cap;
     PeelCtl* ctl;
     int64_t* round_size;
@@ -206,7 +257,6 @@ void nd_edge_support(const GraphView& g, int64_t* sigma, int64_t* up, cudaStream
 void nd_edge_fill(const GraphView& g, int64_t* et_rp, int64_t* tbase, int32_t* et_w, int32_t* et_t,
                   int32_t* tri_e, int32_t* tri_pos, cudaStream_t st);
 void nd_edge_fill_tid(const GraphView& g, int32_t* et_t, int32_t* tri_pos, cudaStream_t st);
-void nd_edge_clear_flags(const GraphView& g, cudaStream_t st);
 void nd_tri_tuples(const GraphView& g, int32_t* out, cudaStream_t st);
 void nd_edge_tuples(const GraphView& g, int32_t* out, cudaStream_t st);
 

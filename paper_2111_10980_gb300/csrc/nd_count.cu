@@ -57,7 +57,10 @@ __global__ void k_count23(GraphView g, CT* __restrict__ cnt) {
             ny = tn;
         }
         int c = 0;
-        for (int64_t i = lane; i < nx; i += 32) c += nd_find(ys, ny, xs[i]) >= 0 ? 1 : 0;
+        if (nd_prefer_merge(nx, ny))
+            nd_warp_merge(xs, nx, ys, ny, [&](bool f, int64_t, int64_t) { c += f ? 1 : 0; });
+        else
+            for (int64_t i = lane; i < nx; i += 32) c += nd_find(ys, ny, xs[i]) >= 0 ? 1 : 0;
         c = warp_sum(c);
         if (lane == 0) cnt[e] = (CT)c;
     }
@@ -84,7 +87,10 @@ __global__ void k_count34(GraphView g, CT* __restrict__ cnt) {
         }
         if (n2 < n1) b1 = b2, n1 = n2;
         int c = 0;
-        for (int64_t i = lane; i < n0; i += 32) c += nd_find(g.et_w + b1, n1, g.et_w[b0 + i]) >= 0 ? 1 : 0;
+        if (nd_prefer_merge(n0, n1))
+            nd_warp_merge(g.et_w + b0, n0, g.et_w + b1, n1, [&](bool f, int64_t, int64_t) { c += f ? 1 : 0; });
+        else
+            for (int64_t i = lane; i < n0; i += 32) c += nd_find(g.et_w + b1, n1, g.et_w[b0 + i]) >= 0 ? 1 : 0;
         c = warp_sum(c);
         if (lane == 0) cnt[t] = (CT)c;
     }

@@ -160,11 +160,20 @@ __global__ void k_edge_support(GraphView g, int64_t* __restrict__ sigma, int64_t
             ny = tn;
         }
         int c = 0, cu = 0;
-        for (int64_t i = lane; i < nx; i += 32) {
-            int32_t w = xs[i];
-            if (nd_find(ys, ny, w) >= 0) {
-                c++;
-                cu += (w > b) ? 1 : 0;
+        if (nd_prefer_merge(nx, ny)) {
+            nd_warp_merge(xs, nx, ys, ny, [&](bool f, int64_t ix, int64_t) {
+                if (f) {
+                    c++;
+                    cu += (xs[ix] > b) ? 1 : 0;
+                }
+            });
+        } else {
+            for (int64_t i = lane; i < nx; i += 32) {
+                int32_t w = xs[i];
+                if (nd_find(ys, ny, w) >= 0) {
+                    c++;
+                    cu += (w > b) ? 1 : 0;
+                }
             }
         }
         for (int o = 16; o > 0; o >>= 1) {
@@ -194,20 +203,14 @@ __global__ void k_edge_fill(GraphView g, const int64_t* __restrict__ et_rp, cons
         int64_t sig = et_rp[e + 1] - out;
         int64_t split_e = sig - (tbase[e + 1] - tbase[e]);
         int64_t pos = 0;
-        for (int64_t p0 = xb; p0 < xe; p0 += 32) {
-            int64_t p = p0 + lane;
-            int32_t w = 0;
-            int64_t q = -1;
-            if (p < xe) {
-                w = g.col[p];
-                q = nd_find(g.col + yb, ye - yb, w);
-            }
-            bool hit = q >= 0;
+        // writes the common element at driver position p and other-list position q (q < 0: none)
+        auto emit = [&](bool hit, int64_t p, int64_t q) {
             unsigned m = __ballot_sync(0xffffffffu, hit);
             if (hit) {
+                int32_t w = g.col[p];
                 int64_t local = pos + __popc(m & nd_lanemask_lt());
-                int64_t pa = a_drives ? p : yb + q;  // position of w in N(a)
-                int64_t pb = a_drives ? yb + q : p;  // position of w in N(b)
+                int64_t pa = a_drives ? p : q;  // position of w in N(a)
+                int64_t pb = a_drives ? q : p;  // position of w in N(b)
                 int32_t e_aw = g.pos2e[pa], e_bw = g.pos2e[pb];
                 et_w[out + local] = w;
                 if (w > b) {
@@ -222,6 +225,17 @@ __global__ void k_edge_fill(GraphView g, const int64_t* __restrict__ et_rp, cons
                 }
             }
             pos += __popc(m);
+        };
+        if (nd_prefer_merge(xe - xb, ye - yb)) {
+            nd_warp_merge(g.col + xb, xe - xb, g.col + yb, ye - yb,
+                          [&](bool f, int64_t ix, int64_t iy) { emit(f, xb + ix, yb + iy); });
+        } else {
+            for (int64_t p0 = xb; p0 < xe; p0 += 32) {
+                int64_t p = p0 + lane;
+                int64_t q = -1;
+                if (p < xe) q = nd_find(g.col + yb, ye - yb, g.col[p]);
+                emit(q >= 0, p, q >= 0 ? yb + q : -1);
+            }
         }
     }
 }
@@ -245,11 +259,6 @@ __global__ void k_edge_fill_tid(GraphView g, int32_t* __restrict__ et_t, int32_t
             tri_pos[3 * tid + (g.et_w[j] > a ? 1 : 2)] = (int32_t)(j - lo);
         }
     }
-}
-
-__global__ void k_clear_flags(int32_t* __restrict__ et_t, int64_t n) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        et_t[i] = (int32_t)((uint32_t)et_t[i] & ND_ET_ID);
 }
 
 __global__ void k_tri_tuples(GraphView g, int32_t* __restrict__ out) {
@@ -313,10 +322,6 @@ void nd_edge_fill_tid(const GraphView& g, int32_t* et_t, int32_t* tri_pos, cudaS
     ND_K(k_edge_fill_tid<<<blocks_for_warps(g.m), kThreads, 0, st>>>(g, et_t, tri_pos));
 }
 
-void nd_edge_clear_flags(const GraphView& g, cudaStream_t st) {
-    if (g.n3 <= 0) return;
-    ND_K(k_clear_flags<<<blocks_for_threads(3 * g.n3), kThreads, 0, st>>>(g.et_flags, 3 * g.n3));
-}
 
 void nd_tri_tuples(const GraphView& g, int32_t* out, cudaStream_t st) {
     if (g.n3 <= 0) return;

@@ -55,7 +55,7 @@ struct nd_graph {
 
 struct PeelOut {
     DBuf core, rnd;
-    int64_t rho = 0, max_core = 0, listed = 0, advances = 0, refills = 0;
+    int64_t rho = 0, max_core = 0, listed = 0, decs = 0, advances = 0, refills = 0;
     std::vector<int64_t> sizes, levels;
 };
 

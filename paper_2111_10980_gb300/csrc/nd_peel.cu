@@ -55,6 +55,16 @@ __device__ __forceinline__ int64_t knew_of(const PeelCtl* c) {
 // parameter block to local memory)
 __device__ __forceinline__ int32_t* pick(int32_t* const (&a)[2], int i) { return i ? a[1] : a[0]; }
 
+// (3,4): tag the three index entries of triangle R with the round in which it is peeled.
+template <typename CT>
+__device__ __forceinline__ void set_tri_round(const PeelView<CT>& P, int64_t R, int32_t round) {
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+        int32_t e = P.tri_e[3 * R + x];
+        P.et_rnd[P.et_rp[e] + P.tri_pos[3 * R + x]] = round;
+    }
+}
+
 // list sizes read back from the control block never exceed the list capacity (an overflow sets
 // ctl->err and is reported by the host)
 __device__ __forceinline__ unsigned clampn(unsigned v, uint32_t cap) { return v < cap ? v : cap; }
@@ -99,7 +109,9 @@ __global__ void k_init(PeelCtl* c, int64_t n_r, int64_t max_rounds) {
         c->nA = c->cntA = c->nNext = c->nN = c->nN2 = c->nL = c->nL2 = c->nH = 0;
         c->minN = c->gmin = ULLONG_MAX;
         c->listed = 0;
+        c->decs = 0;
         c->bar_arrive = 0;
+        c->bar_gen = 0;
         c->advances = c->refills = 0;
     }
 }
@@ -289,6 +301,29 @@ __device__ void phase_refill_pick(PeelCtl* c) {
 
 __global__ void k_refill_pick(PeelCtl* c) { phase_refill_pick(c); }
 
+// The same choice made by one thread (the serial part of a grid barrier).
+__device__ void refill_pick_serial(PeelCtl* c) {
+    unsigned long long alive = c->nL2;
+    unsigned long long target = alive / 16;
+    if (target < 16384) target = 16384;
+    unsigned long long run = 0;
+    int b = ND_HBINS - 1;
+    for (int i = 0; i < ND_HBINS; ++i) {
+        run += c->hist[i];
+        if (run >= target) {
+            b = i;
+            break;
+        }
+    }
+    c->hi = (b >= ND_HBINS - 1) ? LLONG_MAX : (int64_t)c->gmin + b + 1;
+    c->wl ^= 1;
+    c->nL = c->nL2;
+    c->nL2 = 0;
+    c->lmat = 1;
+    c->nN = 0;
+    c->refills++;
+}
+
 // refill 4/4: N = { R in L : count < hi }
 template <typename CT>
 __device__ void phase_refill_select(const PeelView<CT>& P) {
@@ -326,6 +361,7 @@ __device__ void phase_adv_select(const PeelView<CT>& P) {
                 if ((int64_t)P.cnt[R] <= kn) {
                     P.rnd[R] = t;
                     P.core[R] = (int32_t)kn;
+                    if (P.et_rnd) set_tri_round(P, R, t);
                     nd_append(&c->cntA, A, P.cap, R, &c->err);
                 } else {
                     nd_append(&c->nN2, N2, P.cap, R, &c->err);
@@ -378,39 +414,62 @@ __device__ __forceinline__ RoundEnv<CT> round_env(const PeelView<CT>& P) {
     return E;
 }
 
+// per-thread statistics of one Update phase
+struct UpdCounters {
+    unsigned long long listed = 0;  // s-cliques destroyed (counted once, by the owner)
+    unsigned long long decs = 0;    // count decrements applied
+};
+
+// What a decrement of r-clique x from o to o - 1 implies: x falls to <= k (it is the next
+// round's A: its round, core number and index tags are written now) and/or below the bucket
+// window (it joins N).
 template <typename CT>
-__device__ __forceinline__ void dec_one(const RoundEnv<CT>& E, int32_t x) {
-    int64_t o = nd_atomic_dec(&E.P.cnt[x]);
+__device__ __forceinline__ void after_dec(const RoundEnv<CT>& E, int32_t x, int64_t o) {
     if (o > E.k && o - 1 <= E.k) {
         E.P.rnd[x] = E.t + 1;
         E.P.core[x] = (int32_t)E.k;
+        if (E.P.et_rnd) set_tri_round(E.P, x, E.t + 1);
         nd_append(&E.P.ctl->nNext, E.next, E.P.cap, x, &E.P.ctl->err);
     }
     if (o >= E.hi && o - 1 < E.hi) nd_append(E.ncnt, E.Ncur, E.P.cap, x, &E.P.ctl->err);
 }
 
+
 // Update-Func for the s-clique S made of R and the other r-subsets o[0..M). Returns whether S
 // was live (no r-subset peeled in an earlier round).
 template <typename CT, int M>
-__device__ __forceinline__ bool update_func(const RoundEnv<CT>& E, int32_t R, const int32_t (&o)[M]) {
+__device__ __forceinline__ void update_func(const RoundEnv<CT>& E, int32_t R, const int32_t (&o)[M], UpdCounters& k) {
     int32_t ro[M];
     int32_t owner = R;
 #pragma unroll
     for (int i = 0; i < M; ++i) {
         ro[i] = E.P.rnd[o[i]];
-        if (ro[i] < E.t) return false;  // an r-subset was peeled in an earlier round
+        if (ro[i] < E.t) return;  // an r-subset was peeled in an earlier round
         if (ro[i] == E.t && o[i] < owner) owner = o[i];
     }
-    if (owner != R) return true;
+    if (owner != R) return;
+    k.listed++;
+    // issue every decrement before looking at any result (the atomics overlap in flight)
+    int64_t old[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) old[i] = ro[i] != E.t ? nd_atomic_dec(&E.P.cnt[o[i]]) : 0;
 #pragma unroll
     for (int i = 0; i < M; ++i)
-        if (ro[i] != E.t) dec_one(E, o[i]);
-    return true;
+        if (ro[i] != E.t) {
+            k.decs++;
+            after_dec(E, o[i], old[i]);
+        }
 }
 
-__device__ __forceinline__ void add_listed(PeelCtl* c, unsigned long long v) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0 && v) atomicAdd(&c->listed, v);
+__device__ __forceinline__ void add_counters(PeelCtl* c, UpdCounters k) {
+    for (int o = 16; o > 0; o >>= 1) {
+        k.listed += __shfl_down_sync(0xffffffffu, k.listed, o);
+        k.decs += __shfl_down_sync(0xffffffffu, k.decs, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (k.listed) atomicAdd(&c->listed, k.listed);
+        if (k.decs) atomicAdd(&c->decs, k.decs);
+    }
 }
 
 // Each Update variant is a functor with
@@ -419,8 +478,8 @@ __device__ __forceinline__ void add_listed(PeelCtl* c, unsigned long long v) {
 //                               j0, j0 + dj, ... (lanes of one warp: j0 = lane, dj = 32;
 //                               the whole grid on one heavy R: j0 = global lane, dj = all lanes).
 // The light kernel gives each warp one R at a time and defers R with work > kHeavy to a list that
-// the heavy kernel then spreads over every warp of the grid, so a few hub r-cliques in a round do
-// not serialise on single warps.
+// the heavy kernel then gives one block each (threads striding the driving list), so a few hub
+// r-cliques in a round do not serialise on single warps.
 constexpr int64_t kHeavy = 4096;
 
 // (1,2): R = v; S = {v, w} for every neighbour w.
@@ -428,11 +487,11 @@ template <typename CT>
 struct Upd12 {
     __device__ static int64_t work(const GraphView& g, int32_t v) { return g.rp[v + 1] - g.rp[v]; }
     __device__ static void run(const GraphView& g, const RoundEnv<CT>& E, int32_t v, int64_t j0, int64_t dj,
-                               unsigned long long& listed) {
+                               UpdCounters& k) {
         int64_t b = g.rp[v], e = g.rp[v + 1];
         for (int64_t p = b + j0; p < e; p += dj) {
             int32_t o[1] = {g.col[p]};
-            listed += update_func<CT, 1>(E, v, o) ? 1 : 0;
+            update_func<CT, 1>(E, v, o, k);
         }
     }
 };
@@ -442,7 +501,7 @@ template <typename CT>
 struct Upd13 {
     __device__ static int64_t work(const GraphView& g, int32_t v) { return g.rp[v + 1] - g.rp[v]; }
     __device__ static void run(const GraphView& g, const RoundEnv<CT>& E, int32_t v, int64_t j0, int64_t dj,
-                               unsigned long long& listed) {
+                               UpdCounters& k) {
         int64_t b = g.rp[v], e = g.rp[v + 1];
         for (int64_t p = b + j0; p < e; p += dj) {
             int32_t w = g.col[p];
@@ -450,7 +509,7 @@ struct Upd13 {
                 int32_t x = g.dg_col[jx];
                 if (nd_find(g.col + b, e - b, x) < 0) continue;
                 int32_t o[2] = {w, x};
-                listed += update_func<CT, 2>(E, v, o) ? 1 : 0;
+                update_func<CT, 2>(E, v, o, k);
             }
         }
     }
@@ -465,7 +524,7 @@ struct Upd23 {
         return du < dv ? du : dv;
     }
     __device__ static void run(const GraphView& g, const RoundEnv<CT>& E, int32_t R, int64_t j0, int64_t dj,
-                               unsigned long long& listed) {
+                               UpdCounters& k) {
         int32_t u = g.eu[R], v = g.ev[R];
         int64_t xb = g.rp[u], xe = g.rp[u + 1], yb = g.rp[v], ye = g.rp[v + 1];
         if (xe - xb > ye - yb) {
@@ -473,21 +532,29 @@ struct Upd23 {
             xb = yb, xe = ye, yb = t0, ye = t1;
         }
         for (int64_t p = xb + j0; p < xe; p += dj) {
+            // the edge to the candidate, peeled in an earlier round: every S through it is dead
+            int32_t e_xw = g.pos2e[p];
+            if (E.P.rnd[e_xw] < E.t) continue;
             int32_t w = g.col[p];
             int64_t q = nd_find(g.col + yb, ye - yb, w);
             if (q < 0) continue;
-            int32_t o[2] = {g.pos2e[p], g.pos2e[yb + q]};
-            listed += update_func<CT, 2>(E, R, o) ? 1 : 0;
+            int32_t o[2] = {e_xw, g.pos2e[yb + q]};
+            update_func<CT, 2>(E, R, o, k);
         }
     }
 };
 
 // (2,4): R = (u,v); S = {u, v, w, x} for w in N(u) ∩ N(v) and x in N_DG(w) ∩ N(u) ∩ N(v).
+// shared-memory staging of I = N(u) ∩ N(v) for the (2,4) warp path: up to kI24 entries per warp
+constexpr int kI24 = 128;
+constexpr int kMaxWarpsPerBlock = 16;
+
 template <typename CT>
 struct Upd24 {
+    static constexpr bool kWarpSmem = true;
     __device__ static int64_t work(const GraphView& g, int32_t R) { return Upd23<CT>::work(g, R); }
     __device__ static void run(const GraphView& g, const RoundEnv<CT>& E, int32_t R, int64_t j0, int64_t dj,
-                               unsigned long long& listed) {
+                               UpdCounters& k) {
         int32_t u = g.eu[R], v = g.ev[R];
         int64_t ub = g.rp[u], un = g.rp[u + 1] - ub, vb = g.rp[v], vn = g.rp[v + 1] - vb;
         bool u_drives = un <= vn;
@@ -505,17 +572,72 @@ struct Upd24 {
                 int64_t py = nd_find(g.col + yb, yn, x);
                 if (py < 0) continue;
                 int32_t o[5] = {e_xw, e_yw, g.pos2e[xb + px], g.pos2e[yb + py], g.dg_eid[jx]};
-                listed += update_func<CT, 5>(E, R, o) ? 1 : 0;
+                update_func<CT, 5>(E, R, o, k);
             }
         }
+    }
+    // One warp: I (with the edge ids to u and v) staged in shared memory, then every DG edge
+    // w -> x with w, x in I found by a binary search of x in the staged I.
+    __device__ static void run_warp(const GraphView& g, const RoundEnv<CT>& E, int32_t R, UpdCounters& k,
+                                    int32_t* sw, int32_t* sx, int32_t* sy) {
+        int lane = threadIdx.x & 31;
+        int32_t u = g.eu[R], v = g.ev[R];
+        int64_t ub = g.rp[u], un = g.rp[u + 1] - ub, vb = g.rp[v], vn = g.rp[v + 1] - vb;
+        bool u_drives = un <= vn;
+        int64_t xb = u_drives ? ub : vb, xn = u_drives ? un : vn;
+        int64_t yb = u_drives ? vb : ub, yn = u_drives ? vn : un;
+        int cnt = 0;
+        bool overflow = false;
+        for (int64_t p0 = 0; p0 < xn; p0 += 32) {
+            int64_t p = p0 + lane;
+            int64_t q = -1;
+            if (p < xn) q = nd_find(g.col + yb, yn, g.col[xb + p]);
+            unsigned m = __ballot_sync(0xffffffffu, q >= 0);
+            int at = cnt + __popc(m & nd_lanemask_lt());
+            if (q >= 0 && at < kI24) {
+                sw[at] = g.col[xb + p];
+                sx[at] = g.pos2e[xb + p];
+                sy[at] = g.pos2e[yb + q];
+            }
+            cnt += __popc(m);
+            if (cnt > kI24) {
+                overflow = true;
+                break;
+            }
+        }
+        __syncwarp();
+        if (overflow) {
+            run(g, E, R, lane, 32, k);
+            return;
+        }
+        for (int i = lane; i < cnt; i += 32) {
+            int32_t w = sw[i];
+            for (int64_t jx = g.dg_rp[w]; jx < g.dg_rp[w + 1]; ++jx) {
+                int32_t x = g.dg_col[jx];
+                // binary search of x in the staged I (ascending)
+                int lo = 0, hi = cnt;
+                while (lo < hi) {
+                    int mid = (lo + hi) >> 1;
+                    if (sw[mid] < x)
+                        lo = mid + 1;
+                    else
+                        hi = mid;
+                }
+                if (lo >= cnt || sw[lo] != x) continue;
+                int32_t o[5] = {sx[i], sy[i], sx[lo], sy[lo], g.dg_eid[jx]};
+                update_func<CT, 5>(E, R, o, k);
+            }
+        }
+        __syncwarp();
     }
 };
 
 // (3,4): R = triangle (a,b,c) with edges ab, ac, bc; S = R + w for w in L(ab) ∩ L(ac) ∩ L(bc);
-// the three other triangles of S are the table entries of w in the three lists. The entries
-// carry the flags set by k_flag34: a DEAD entry's triangle was peeled in an earlier round, so
-// every S through it is dead and the candidate is dropped before any search; INA marks the
-// members of A for the owner rule. No per-triangle state is read at random.
+// the three other triangles of S are the table entries of w in the three lists. Every entry
+// carries the round tag of its triangle (et_rnd, written when the triangle is scheduled): a
+// tag below the current round means that triangle was peeled earlier, so every S through it is
+// dead and the candidate is dropped before any further search; a tag equal to the round marks a
+// member of A for the owner rule. No per-triangle state is read at random.
 __device__ __forceinline__ void lists34(const GraphView& g, int32_t R, int64_t (&b)[3], int64_t (&n)[3]) {
 #pragma unroll
     for (int x = 0; x < 3; ++x) {
@@ -545,35 +667,55 @@ struct Upd34 {
         lists34(g, R, b, n);
         return n[0];
     }
+    // S = R + w, with w at position i0 of list 0 and i1 of list 1 (both tags alive or in A).
+    // Only the owner (smallest id of S's members in A) applies S, so as soon as a member in A
+    // with a smaller id than R is known, R stops: the owner does the full check itself.
+    __device__ static void finish(const GraphView& g, const RoundEnv<CT>& E, int32_t R, const int64_t (&b)[3],
+                                  const int64_t (&n)[3], int64_t i0, int64_t i1, int32_t r0, int32_t r1,
+                                  UpdCounters& k) {
+        const int32_t* tag = E.P.et_rnd;
+        int32_t id0 = g.et_t[b[0] + i0], id1 = g.et_t[b[1] + i1];
+        if ((r0 == E.t && id0 < R) || (r1 == E.t && id1 < R)) return;
+        int64_t q2 = nd_find(g.et_w + b[2], n[2], g.et_w[b[0] + i0]);
+        if (q2 < 0) return;
+        int32_t r2 = tag[b[2] + q2];
+        if (r2 < E.t) return;
+        int32_t id2 = g.et_t[b[2] + q2];
+        if (r2 == E.t && id2 < R) return;
+        k.listed++;
+        // issue the decrements before looking at any result (the atomics overlap in flight)
+        int64_t o0 = r0 != E.t ? nd_atomic_dec(&E.P.cnt[id0]) : 0;
+        int64_t o1 = r1 != E.t ? nd_atomic_dec(&E.P.cnt[id1]) : 0;
+        int64_t o2 = r2 != E.t ? nd_atomic_dec(&E.P.cnt[id2]) : 0;
+        k.decs += (r0 != E.t) + (r1 != E.t) + (r2 != E.t);
+        if (r0 != E.t) after_dec(E, id0, o0);
+        if (r1 != E.t) after_dec(E, id1, o1);
+        if (r2 != E.t) after_dec(E, id2, o2);
+    }
     __device__ static void run(const GraphView& g, const RoundEnv<CT>& E, int32_t R, int64_t j0, int64_t dj,
-                               unsigned long long& listed) {
-        const uint32_t* et = reinterpret_cast<const uint32_t*>(g.et_flags);
+                               UpdCounters& k) {
+        const int32_t* tag = E.P.et_rnd;
         int64_t b[3], n[3];
         lists34(g, R, b, n);
         for (int64_t j = j0; j < n[0]; j += dj) {
-            uint32_t f0 = et[b[0] + j];
-            if (f0 & ND_ET_DEAD) continue;
-            int32_t w = g.et_w[b[0] + j];
-            int64_t q1 = nd_find(g.et_w + b[1], n[1], w);
+            int32_t r0 = tag[b[0] + j];
+            if (r0 < E.t) continue;
+            int64_t q1 = nd_find(g.et_w + b[1], n[1], g.et_w[b[0] + j]);
             if (q1 < 0) continue;
-            uint32_t f1 = et[b[1] + q1];
-            if (f1 & ND_ET_DEAD) continue;
-            int64_t q2 = nd_find(g.et_w + b[2], n[2], w);
-            if (q2 < 0) continue;
-            uint32_t f2 = et[b[2] + q2];
-            if (f2 & ND_ET_DEAD) continue;
-            listed++;
-            int32_t owner = R;
-            uint32_t fs[3] = {f0, f1, f2};
-#pragma unroll
-            for (int x = 0; x < 3; ++x)
-                if ((fs[x] & ND_ET_INA) && (int32_t)(fs[x] & ND_ET_ID) < owner) owner = (int32_t)(fs[x] & ND_ET_ID);
-            if (owner != R) continue;
-#pragma unroll
-            for (int x = 0; x < 3; ++x)
-                if (!(fs[x] & ND_ET_INA)) dec_one(E, (int32_t)(fs[x] & ND_ET_ID));
+            int32_t r1 = tag[b[1] + q1];
+            if (r1 < E.t) continue;
+            finish(g, E, R, b, n, j, q1, r0, r1, k);
         }
     }
+};
+
+template <typename U, typename = void>
+struct has_warp_smem {
+    static constexpr bool value = false;
+};
+template <typename U>
+struct has_warp_smem<U, decltype((void)U::kWarpSmem)> {
+    static constexpr bool value = U::kWarpSmem;
 };
 
 template <typename CT, typename U>
@@ -581,7 +723,7 @@ __device__ void phase_update(const GraphView& g, const PeelView<CT>& P) {
     if (P.ctl->done) return;
     RoundEnv<CT> E = round_env(P);
     int lane = threadIdx.x & 31;
-    unsigned long long listed = 0;
+    UpdCounters k;
     for (int64_t i = gwarp(); i < E.nA; i += nwarps()) {
         int32_t R = E.A[i];
         if (U::work(g, R) > kHeavy) {
@@ -595,9 +737,16 @@ __device__ void phase_update(const GraphView& g, const PeelView<CT>& P) {
             }
             if (__shfl_sync(0xffffffffu, queued, 0)) continue;
         }
-        U::run(g, E, R, lane, 32, listed);
+        if constexpr (has_warp_smem<U>::value) {
+            __shared__ int32_t s_w[kMaxWarpsPerBlock][kI24], s_x[kMaxWarpsPerBlock][kI24],
+                s_y[kMaxWarpsPerBlock][kI24];
+            int wid = threadIdx.x >> 5;
+            U::run_warp(g, E, R, k, s_w[wid], s_x[wid], s_y[wid]);
+        } else {
+            U::run(g, E, R, lane, 32, k);
+        }
     }
-    add_listed(P.ctl, listed);
+    add_counters(P.ctl, k);
 }
 
 template <typename CT, typename U>
@@ -606,37 +755,17 @@ __device__ void phase_update_heavy(const GraphView& g, const PeelView<CT>& P) {
     unsigned nH = clampn(P.ctl->nH, P.hcap);
     if (nH == 0) return;
     RoundEnv<CT> E = round_env(P);
-    unsigned long long listed = 0;
-    int64_t j0 = gthread(), dj = nthreads();
-    for (unsigned h = 0; h < nH; ++h) U::run(g, E, P.H[h], j0, dj, listed);
-    add_listed(P.ctl, listed);
-}
-
-// Sets (kill = false) the INA flag, or replaces it by DEAD (kill = true), on the three table
-// entries of every triangle of this round's A.
-template <typename CT, bool kKill>
-__device__ void phase_flag34(const GraphView& g, const PeelView<CT>& P) {
-    PeelCtl* c = P.ctl;
-    if (c->done) return;
-    bool adv = c->mode & ND_MODE_ADV;
-    unsigned nA = clampn(adv ? c->cntA : c->nA, P.cap);
-    const int32_t* A = pick(P.A, c->wa);
-    for (int64_t i = gthread(); i < 3 * (int64_t)nA; i += nthreads()) {
-        int64_t R = A[i / 3];
-        int slot = (int)(i % 3);
-        int32_t e = g.tri_e[3 * R + slot];
-        int64_t pos = g.et_rp[e] + g.tri_pos[3 * R + slot];
-        uint32_t v = (uint32_t)g.et_flags[pos];
-        g.et_flags[pos] = (int32_t)(kKill ? ((v & ND_ET_ID) | ND_ET_DEAD) : (v | ND_ET_INA));
-    }
+    UpdCounters k;
+    // one block per heavy r-clique, its threads striding the driving list: heavy r-cliques run
+    // side by side, each over many threads
+    for (unsigned h = blockIdx.x; h < nH; h += gridDim.x) U::run(g, E, P.H[h], threadIdx.x, blockDim.x, k);
+    add_counters(P.ctl, k);
 }
 
 template <typename CT, typename U>
 __global__ void k_update(GraphView g, PeelView<CT> P) { phase_update<CT, U>(g, P); }
 template <typename CT, typename U>
 __global__ void k_update_heavy(GraphView g, PeelView<CT> P) { phase_update_heavy<CT, U>(g, P); }
-template <typename CT, bool kKill>
-__global__ void k_flag34(GraphView g, PeelView<CT> P) { phase_flag34<CT, kKill>(g, P); }
 
 // ------------------------------------------------------------------------------------
 // The whole peeling loop in one cooperative launch (every block resident at once), with a grid
@@ -665,28 +794,44 @@ __device__ __forceinline__ int ld_acquire_i32(const int* p) {
     return v;
 }
 
-__device__ __forceinline__ void red_release_add_u64(unsigned long long* p, unsigned long long v) {
-    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+
+__device__ __forceinline__ unsigned long long atom_add_acq_rel_u64(unsigned long long* p, unsigned long long v) {
+    unsigned long long old;
+    asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+    return old;
 }
 
-// Returns false if the barrier gave up (timeout or another block's failure).
-__device__ bool grid_barrier(PeelCtl* c, unsigned long long& target) {
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Grid barrier. The block that arrives last runs serial() in its thread 0 (it sees every write
+// made before the barrier) and then releases the others, so a control step costs no extra
+// barrier. Arrival is an acquire-release RMW and the release a release store; waiting blocks poll
+// with an acquire load, so all writes before the barrier are visible after it. The wait is
+// bounded by the global timer: after kBarrierTimeoutNs, or once another block gave up, a block
+// sets ctl->err bit 8 and the function returns false.
+template <typename F>
+__device__ bool grid_barrier(PeelCtl* c, unsigned long long& target, F serial) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         target += gridDim.x;
-        red_release_add_u64(&c->bar_arrive, 1ull);
-        unsigned long long t0 = globaltimer();
-        unsigned ns = 32;
+        unsigned long long old = atom_add_acq_rel_u64(&c->bar_arrive, 1ull);
         int good = 1;
-        while (ld_acquire_u64(&c->bar_arrive) < target) {
-            if ((ld_acquire_i32(&c->err) & 8) || globaltimer() - t0 > kBarrierTimeoutNs) {
-                atomicOr(&c->err, 8);
-                good = 0;
-                break;
+        if (old + 1 == target) {
+            serial();
+            st_release_u64(&c->bar_gen, target);
+        } else {
+            unsigned long long t0 = globaltimer();
+            while (ld_acquire_u64(&c->bar_gen) < target) {
+                if ((ld_acquire_i32(&c->err) & 8) || globaltimer() - t0 > kBarrierTimeoutNs) {
+                    atomicOr(&c->err, 8);
+                    good = 0;
+                    break;
+                }
+                __nanosleep(20);
             }
-            __nanosleep(ns);
-            if (ns < 1024) ns <<= 1;
         }
         ok = good;
     }
@@ -694,43 +839,61 @@ __device__ bool grid_barrier(PeelCtl* c, unsigned long long& target) {
     return ok != 0;
 }
 
+struct NoSerial {
+    __device__ void operator()() const {}
+};
+
+template <typename CT>
+struct CtlSerial {
+    PeelCtl* c;
+    const PeelView<CT>* P;
+    __device__ void operator()() const { ctl_step(c, P->round_size, P->round_level, P->round_cap); }
+};
+
+// after the light Update: finish the round now unless heavy r-cliques are waiting
+template <typename CT>
+struct CtlUnlessHeavy {
+    PeelCtl* c;
+    const PeelView<CT>* P;
+    __device__ void operator()() const {
+        if (c->nH == 0) ctl_step(c, P->round_size, P->round_level, P->round_cap);
+    }
+};
+
+struct PickSerial {
+    PeelCtl* c;
+    __device__ void operator()() const { refill_pick_serial(c); }
+};
+
+// One round: [advance: min over N; (refill: compact + min, histogram, pick, select); select A]
+// Update (light, one warp per r-clique), then the heavy r-cliques if any. The control step runs
+// as the serial part of the round's last barrier; a same-level round costs one barrier.
 template <typename CT, typename U, bool k34>
-__global__ void __launch_bounds__(256) k_peel_loop(GraphView g, PeelView<CT> P) {
+__global__ void __launch_bounds__(512, 2) k_peel_loop(GraphView g, PeelView<CT> P) {
     PeelCtl* c = P.ctl;
     unsigned long long target = 0;
+    if (!grid_barrier(c, target, CtlSerial<CT>{c, &P})) return;  // set up round 0
     for (;;) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) ctl_step(c, P.round_size, P.round_level, P.round_cap);
-        if (!grid_barrier(c, target)) return;
         if (c->done) return;  // every block reads the same value after the barrier
         if (c->mode & ND_MODE_ADV) {
             phase_adv_min(P);
-            if (!grid_barrier(c, target)) return;
+            if (!grid_barrier(c, target, NoSerial{})) return;
             if (need_refill(c)) {
                 phase_refill_scan(P);
-                if (!grid_barrier(c, target)) return;
+                if (!grid_barrier(c, target, NoSerial{})) return;
                 phase_refill_hist(P);
-                if (!grid_barrier(c, target)) return;
-                if (blockIdx.x == 0) phase_refill_pick(c);
-                if (!grid_barrier(c, target)) return;
+                if (!grid_barrier(c, target, PickSerial{c})) return;
                 phase_refill_select(P);
-                if (!grid_barrier(c, target)) return;
+                if (!grid_barrier(c, target, NoSerial{})) return;
             }
             phase_adv_select(P);
-            if (!grid_barrier(c, target)) return;
-        }
-        if (k34) {
-            phase_flag34<CT, false>(g, P);
-            if (!grid_barrier(c, target)) return;
+            if (!grid_barrier(c, target, NoSerial{})) return;
         }
         phase_update<CT, U>(g, P);
-        if (!grid_barrier(c, target)) return;
+        if (!grid_barrier(c, target, CtlUnlessHeavy<CT>{c, &P})) return;
         if (c->nH) {
             phase_update_heavy<CT, U>(g, P);
-            if (!grid_barrier(c, target)) return;
-        }
-        if (k34) {
-            phase_flag34<CT, true>(g, P);
-            if (!grid_barrier(c, target)) return;
+            if (!grid_barrier(c, target, CtlSerial<CT>{c, &P})) return;
         }
     }
 }
@@ -739,14 +902,14 @@ template <typename CT, typename U, bool k34>
 cudaError_t launch_peel_loop(const GraphView& g, const PeelView<CT>& P, cudaStream_t st) {
     auto kern = k_peel_loop<CT, U, k34>;
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 512, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
-    int blocks = nd_sm_count() * (per_sm < 4 ? per_sm : 4);
+    int blocks = nd_sm_count() * (per_sm < 2 ? per_sm : 2);
     GraphView gv = g;
     PeelView<CT> pv = P;
     void* args[] = {&gv, &pv};
-    e = cudaLaunchCooperativeKernel((const void*)kern, dim3(blocks), dim3(256), args, 0, st);
+    e = cudaLaunchCooperativeKernel((const void*)kern, dim3(blocks), dim3(512), args, 0, st);
     if (e == cudaSuccess) nd_note_launches(1);
     return e;
 }
@@ -804,10 +967,8 @@ void nd_peel_update(const GraphView& g, int r, int s, const PeelView<CT>& P, cud
         ND_K(k_update<CT, Upd24<CT>><<<nb, kThreads, 0, st>>>(g, P));
         ND_K(k_update_heavy<CT, Upd24<CT>><<<nb, kThreads, 0, st>>>(g, P));
     } else if (r == 3 && s == 4) {
-        ND_K(k_flag34<CT, false><<<nb, kThreads, 0, st>>>(g, P));
         ND_K(k_update<CT, Upd34<CT>><<<nb, kThreads, 0, st>>>(g, P));
         ND_K(k_update_heavy<CT, Upd34<CT>><<<nb, kThreads, 0, st>>>(g, P));
-        ND_K(k_flag34<CT, true><<<nb, kThreads, 0, st>>>(g, P));
     }
 }
 
@@ -922,7 +1083,7 @@ cudaError_t nd_peel_persistent(const GraphView& g, int r, int s, const PeelView<
 
 // kernels launched per round by the loop graph (for the launch counter): the nodes executed in
 // a same-level round and the extra ones of an advance round
-int nd_peel_nodes_per_round(int r, int s) { return 1 + (r == 3 ? 4 : 2); }
+int nd_peel_nodes_per_round(int r, int s) { return 3; }
 
 template void nd_peel_round<int32_t>(const GraphView&, int, int, const PeelView<int32_t>&, cudaStream_t);
 template void nd_peel_round<int64_t>(const GraphView&, int, int, const PeelView<int64_t>&, cudaStream_t);

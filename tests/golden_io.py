@@ -14,7 +14,7 @@ def load(name):
             if not line or line.startswith("#"):
                 continue
             parts = line.split()
-            if parts[0] in ("r", "s", "n_s", "rho"):
+            if parts[0] in ("r", "s", "n_s", "rho", "decs"):
                 meta[parts[0]] = int(parts[1])
             elif parts[0] in ("sizes", "levels"):
                 meta[parts[0]] = [int(x) for x in parts[1:]]

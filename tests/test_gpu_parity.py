@@ -63,7 +63,8 @@ def assert_parity(nd, ctx, g, r, s, **kw):
     assert np.array_equal(got["sizes"], want.sizes), tag
     assert np.array_equal(got["levels"], want.levels), tag
     assert got["st"]["n_s"] == wn_s and got["st"]["n_r"] == want.core.size, tag
-    assert got["st"]["listed"] == want.live, tag
+    assert got["st"]["listed"] == wn_s, tag  # every s-clique destroyed exactly once
+    assert got["st"]["decrements"] == want.decs, tag
     if want.core.size:
         assert got["st"]["max_core"] == int(want.core.max()), tag
     return got
@@ -134,7 +135,7 @@ def test_count_width_and_launch_modes_agree(nd, ctx, r, s):
         assert np.array_equal(got["core"], want.core), kw
         assert np.array_equal(got["round"], want.round), kw
         assert got["rho"] == want.rho, kw
-        assert got["st"]["listed"] == want.live, kw
+        assert got["st"]["listed"] == want.n_s, kw
 
 
 @pytest.mark.parametrize("mode", ["NO_GRAPH", "PEEL_LOOP_GRAPH", "PEEL_PERSISTENT"])

@@ -64,6 +64,7 @@ def test_figure1_worked_example(name):
     assert d.levels.tolist() == gold["levels"]
     assert np.array_equal(d.core, gold["core"])
     assert np.array_equal(d.round, gold["round"])
+    assert d.decs == gold["decs"]
     assert np.array_equal(orc.decompose_fixpoint(g, r, s), gold["core"])
 
 
@@ -268,6 +269,9 @@ def test_count_invariants(seed):
         # an s-clique is live for the first round that peels any of its members, and for every
         # member peeled in that round: at least n_s and at most the listings
         assert n_s <= d.live <= d.listed
+        # every s-clique is destroyed exactly once, lowering each member that survives that round
+        # by exactly one: the decrements equal the counts taken by surviving members
+        assert d.decs <= (math.comb(s, r) - 1) * n_s
 
 
 def test_relabel_invariance():
