@@ -59,7 +59,7 @@ def _L():
             lib.orc_count.argtypes = g3 + [ctypes.c_int, ctypes.c_int, i64p, i64p, i64p]
             lib.orc_count.restype = ctypes.c_int
             lib.orc_decompose.argtypes = g3 + [ctypes.c_int, ctypes.c_int, i32p, i32p, i64p, i64p, i64p,
-                                               ctypes.c_int64, i64p, i64p, i64p]
+                                               ctypes.c_int64, i64p, i64p, i64p, i64p]
             lib.orc_decompose.restype = ctypes.c_int
             lib.orc_decompose_fixpoint.argtypes = g3 + [ctypes.c_int, ctypes.c_int, i32p]
             lib.orc_decompose_fixpoint.restype = ctypes.c_int
@@ -125,6 +125,7 @@ class Decomposition:
     n_s: int
     listed: int  # (s-clique, peeled member) pairs re-listed by Update over the whole run
     live: int  # of those, the pairs whose s-clique had no r-subset peeled in an earlier round
+    decs: int  # unit decrements: per live s-clique, its r-subsets outside A (counted once per S)
     extra: dict = field(default_factory=dict)
 
 
@@ -143,12 +144,13 @@ def decompose(g, r: int, s: int) -> Decomposition:
     n_s = ctypes.c_int64()
     listed = ctypes.c_int64()
     live = ctypes.c_int64()
+    decs = ctypes.c_int64()
     _check(_L().orc_decompose(*a, r, s, _p(core, ctypes.c_int32), _p(rnd, ctypes.c_int32), ctypes.byref(rho),
                               _p(sizes, ctypes.c_int64), _p(levels, ctypes.c_int64), cap, ctypes.byref(n_s),
-                              ctypes.byref(listed), ctypes.byref(live)), "decompose")
+                              ctypes.byref(listed), ctypes.byref(live), ctypes.byref(decs)), "decompose")
     t = rho.value
     return Decomposition(core[:nr], rnd[:nr], t, sizes[:t].copy(), levels[:t].copy(), int(n_s.value),
-                         int(listed.value), int(live.value))
+                         int(listed.value), int(live.value), int(decs.value))
 
 
 def decompose_fixpoint(g, r: int, s: int) -> np.ndarray:

@@ -333,9 +333,11 @@ typedef struct {
     int32_t t;
     int64_t L;
     int32_t R[8];
+    int64_t cur;      /* id of R */
     int bad;
     int64_t listed;   /* s-cliques re-listed by Update */
     int64_t live;     /* of those, the ones with no r-subset peeled in an earlier round */
+    int64_t decs;     /* r-subsets outside A whose count a live S lowers (once per S and member) */
 } update_ctx;
 
 /* Update-Func on the s-clique S = R u C (C is an (s-r)-clique in I). */
@@ -366,6 +368,13 @@ static void update_func(update_ctx *U, const int32_t *Cset) {
         if (rq != U->t && rq >= 0) return;
     }
     U->live++;
+    /* the a members of A each list S; count S's surviving members once */
+    {
+        int64_t first = -1;
+        for (int q = 0; q < nsub; ++q)
+            if (U->round[ids[q]] == U->t && (first < 0 || ids[q] < first)) first = ids[q];
+        if (first == U->cur) U->decs += nsub - a;
+    }
     /* subtract 1/a from every r-subset outside A (exactly: L/a on the scaled count) */
     for (int q = 0; q < nsub; ++q)
         if (U->round[ids[q]] != U->t) U->cnt[ids[q]] -= (i128)(U->L / a);
@@ -396,7 +405,7 @@ static void update_grow(update_ctx *U, int32_t *Cset, int depth, const int32_t *
  * Returns 0, -1 (bad r,s), -2 (no memory), -3 (internal inconsistency). */
 int orc_decompose(int32_t n, const int64_t *rp, const int32_t *col, int r, int s, int32_t *core, int32_t *round_out,
                   int64_t *rho_out, int64_t *sizes, int64_t *levels, int64_t cap, int64_t *n_s_out,
-                  int64_t *listed_out, int64_t *live_out) {
+                  int64_t *listed_out, int64_t *live_out, int64_t *decs_out) {
     if (check_rs(r, s)) return -1;
     og g = {n, rp, col};
     rtable T;
@@ -473,6 +482,7 @@ int orc_decompose(int32_t n, const int64_t *rp, const int32_t *col, int r, int s
         for (int64_t q = 0; q < na; ++q) {
             const int32_t *Rt = T.t + A[q] * r;
             memcpy(U.R, Rt, (size_t)r * sizeof(int32_t));
+            U.cur = A[q];
             /* I = intersection of the undirected neighbourhoods of R's vertices */
             int32_t v0 = Rt[0];
             for (int j = 1; j < r; ++j)
@@ -503,6 +513,7 @@ int orc_decompose(int32_t n, const int64_t *rp, const int32_t *col, int r, int s
     if (rho_out) *rho_out = t;
     if (listed_out) *listed_out = U.listed;
     if (live_out) *live_out = U.live;
+    if (decs_out) *decs_out = U.decs;
 done:
     free(c0);
     free(cnt);
