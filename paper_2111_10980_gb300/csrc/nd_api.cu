@@ -197,6 +197,7 @@ static void free_derived(nd_graph* g) {
                     &g->et_w, &g->et_t, &g->tbase, &g->tri_e, &g->tri_pos})
         nd_free(c, *b);
     g->have_base = false;
+    g->edge_mindeg = -1;
     g->orient = -1;
     g->have_tri = false;
     g->n3 = 0;
@@ -600,14 +601,31 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
     cudaStream_t st = c->stream;
     int64_t cap = std::max<int64_t>(n_r, 1);
     int64_t rcap = std::min<int64_t>(n_r, (int64_t)1 << 22) + 1;
-    int64_t hcap = std::min<int64_t>(cap, (int64_t)1 << 20);
-    DBuf ctl, A0, A1, N0, N1, L0, L1, H, rs, rl, etr;
+    // (2,4) stages N(u) ∩ N(v) of every heavy edge: its heavy list holds every edge (the light
+    // path cannot take one back) and each heavy-phase block gets a slice of 5 * (hstage + 1) int32
+    bool staged = r == 2 && s == 4;
+    int64_t hcap = staged ? cap : std::min<int64_t>(cap, (int64_t)1 << 20);
+    int64_t hstage = 0, hslices = 0;
     int rc = ND_OK;
+    if (staged) {
+        if (g->edge_mindeg < 0) {
+            unsigned long long md = 0;
+            ND_TRY(scalar_zero(g));
+            nd_max_edge_mindeg(nd_view(g), (unsigned long long*)g->scal.p, st);
+            ND_TRY(nd_check_launch("peel setup"));
+            ND_TRY(read_back(g, g->scal.p, &md, "peel setup"));
+            g->edge_mindeg = (int64_t)md;
+        }
+        hstage = g->edge_mindeg;
+        hslices = nd_peel_heavy_slices();
+    }
+    DBuf ctl, A0, A1, N0, N1, L0, L1, H, rs, rl, etr, hsc;
     if ((rc = nd_alloc(c, ctl, sizeof(PeelCtl))) || (rc = nd_alloc(c, A0, 4 * cap)) || (rc = nd_alloc(c, A1, 4 * cap)) ||
         (rc = nd_alloc(c, N0, 4 * cap)) || (rc = nd_alloc(c, N1, 4 * cap)) || (rc = nd_alloc(c, L0, 4 * cap)) ||
         (rc = nd_alloc(c, L1, 4 * cap)) || (rc = nd_alloc(c, H, 4 * hcap)) || (rc = nd_alloc(c, rs, 8 * rcap)) ||
-        (rc = nd_alloc(c, rl, 8 * rcap)) || (r == 3 && (rc = nd_alloc(c, etr, 4 * std::max<int64_t>(3 * g->n3, 1))))) {
-        for (DBuf* b : {&ctl, &A0, &A1, &N0, &N1, &L0, &L1, &H, &rs, &rl, &etr}) nd_free(c, *b);
+        (rc = nd_alloc(c, rl, 8 * rcap)) || (r == 3 && (rc = nd_alloc(c, etr, 4 * std::max<int64_t>(3 * g->n3, 1)))) ||
+        (staged && (rc = nd_alloc(c, hsc, 4 * 5 * (hstage + 1) * hslices)))) {
+        for (DBuf* b : {&ctl, &A0, &A1, &N0, &N1, &L0, &L1, &H, &rs, &rl, &etr, &hsc}) nd_free(c, *b);
         return rc;
     }
     PeelView<CT> P;
@@ -622,6 +640,9 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
     P.L[1] = (int32_t*)L1.p;
     P.H = (int32_t*)H.p;
     P.hcap = (uint32_t)hcap;
+    P.hscratch = (int32_t*)hsc.p;
+    P.hstage = hstage;
+    P.hslices = (int32_t)hslices;
     P.cap = (uint32_t)cap;
     P.ctl = (PeelCtl*)ctl.p;
     P.round_size = (int64_t*)rs.p;
@@ -757,7 +778,7 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
             rc = nd_sync(c, "peel record");
         }
     }
-    for (DBuf* b : {&ctl, &A0, &A1, &N0, &N1, &L0, &L1, &H, &rs, &rl, &etr}) nd_free(c, *b);
+    for (DBuf* b : {&ctl, &A0, &A1, &N0, &N1, &L0, &L1, &H, &rs, &rl, &etr, &hsc}) nd_free(c, *b);
     return rc;
 }
 

@@ -204,6 +204,10 @@ struct PeelView {
     int32_t* L[2];
     int32_t* H;      // heavy r-cliques of the current round (capacity hcap)
     uint32_t hcap;
+    // (2,4) heavy phase: hslices scratch slices of 5 * (hstage + 1) int32, one per block
+    int32_t* hscratch;
+    int64_t hstage;
+    int32_t hslices;
     // (3,4) only: the round tag of every triangle-index entry, and what is needed to find the
     // three entries of a triangle (NULL for other (r,s))
     int32_t* et_rnd;
@@ -259,6 +263,9 @@ void nd_edge_fill(const GraphView& g, int64_t* et_rp, int64_t* tbase, int32_t* e
 void nd_edge_fill_tid(const GraphView& g, int32_t* et_t, int32_t* tri_pos, cudaStream_t st);
 void nd_tri_tuples(const GraphView& g, int32_t* out, cudaStream_t st);
 void nd_edge_tuples(const GraphView& g, int32_t* out, cudaStream_t st);
+void nd_max_edge_mindeg(const GraphView& g, unsigned long long* out, cudaStream_t st);
+// blocks of the (2,4) heavy phase that hold a scratch slice; the others skip the phase
+int nd_peel_heavy_slices();
 
 // counting (nd_count.cu): counts into cnt (CT = int32_t or int64_t), zero-initialised
 template <typename CT>

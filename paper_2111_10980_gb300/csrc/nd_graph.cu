@@ -277,7 +277,28 @@ __global__ void k_edge_tuples(GraphView g, int32_t* __restrict__ out) {
     }
 }
 
+// max over edges (u,v) of min(deg u, deg v): a bound on |N(u) ∩ N(v)| for every edge
+__global__ void k_max_edge_mindeg(GraphView g, unsigned long long* __restrict__ out) {
+    unsigned long long best = 0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < g.m; e += (int64_t)gridDim.x * blockDim.x) {
+        int32_t u = g.eu[e], v = g.ev[e];
+        int64_t du = g.rp[u + 1] - g.rp[u], dv = g.rp[v + 1] - g.rp[v];
+        unsigned long long d = (unsigned long long)(du < dv ? du : dv);
+        best = d > best ? d : best;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long y = __shfl_xor_sync(0xffffffffu, best, o);
+        best = y > best ? y : best;
+    }
+    if ((threadIdx.x & 31) == 0 && best) atomicMax(out, best);
+}
+
 }  // namespace
+
+void nd_max_edge_mindeg(const GraphView& g, unsigned long long* out, cudaStream_t st) {
+    if (g.m <= 0) return;
+    ND_K(k_max_edge_mindeg<<<blocks_for_threads(g.m), kThreads, 0, st>>>(g, out));
+}
 
 void nd_validate_csr(const int64_t* rp, const int32_t* col, int32_t n, int64_t nnz, int* err, cudaStream_t st) {
     if (n <= 0) return;

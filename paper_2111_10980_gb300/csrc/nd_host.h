@@ -39,6 +39,7 @@ struct nd_graph {
     bool have_base = false;
     DBuf split, ebase, pos2e, eu, ev;
     int64_t maxdeg = 0;
+    int64_t edge_mindeg = -1;  // max over edges of min(deg u, deg v); -1 until needed
     // orientation
     int orient = -1;
     DBuf dg_rp, dg_col, dg_eid;

@@ -545,41 +545,68 @@ struct Upd23 {
 };
 
 // (2,4): R = (u,v); S = {u, v, w, x} for w in N(u) ∩ N(v) and x in N_DG(w) ∩ N(u) ∩ N(v).
-// shared-memory staging of I = N(u) ∩ N(v) for the (2,4) warp path: up to kI24 entries per warp
-constexpr int kI24 = 128;
+// (2,4) works on I = N(u) ∩ N(v) staged with its edge ids (to u and to v) and the out-lists of
+// its vertices; every DG edge w -> x with w, x in I is a 4-clique S = {u, v, w, x}. The candidate
+// pairs (w, x in N_DG(w)) are expanded flat over the threads through a prefix sum of the
+// out-degrees, and x is looked up in the staged I, so no thread walks a long list serially.
+// An edge whose smaller endpoint degree is at most kI24 is staged in one warp's shared memory;
+// larger ones go to the heavy phase, where one block stages I in a global scratch slice.
+constexpr int kI24 = 96;
 constexpr int kMaxWarpsPerBlock = 16;
+
+struct Stage24 {
+    int32_t* w;     // I, ascending
+    int32_t* ex;    // edge id (driver endpoint, w)
+    int32_t* ey;    // edge id (other endpoint, w)
+    int32_t* base;  // DG out-list start of w (fits int32: at most m < 2^31)
+    int32_t* pre;   // exclusive prefix of the out-degrees, pre[cnt] = total
+};
+
+__device__ __forceinline__ int stage_find(const int32_t* a, int n, int32_t x) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (a[mid] < x)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return (lo < n && a[lo] == x) ? lo : -1;
+}
+
+// index i with pre[i] <= p < pre[i+1]
+__device__ __forceinline__ int stage_owner(const int32_t* pre, int n, int32_t p) {
+    int lo = 0, hi = n;  // invariant: pre[lo] <= p
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (pre[mid] <= p)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
 
 template <typename CT>
 struct Upd24 {
-    static constexpr bool kWarpSmem = true;
+    static constexpr int64_t kHeavyWork = kI24;
+    static constexpr bool kStaged = true;
     __device__ static int64_t work(const GraphView& g, int32_t R) { return Upd23<CT>::work(g, R); }
-    __device__ static void run(const GraphView& g, const RoundEnv<CT>& E, int32_t R, int64_t j0, int64_t dj,
-                               UpdCounters& k) {
-        int32_t u = g.eu[R], v = g.ev[R];
-        int64_t ub = g.rp[u], un = g.rp[u + 1] - ub, vb = g.rp[v], vn = g.rp[v + 1] - vb;
-        bool u_drives = un <= vn;
-        int64_t xb = u_drives ? ub : vb, xn = u_drives ? un : vn;
-        int64_t yb = u_drives ? vb : ub, yn = u_drives ? vn : un;
-        for (int64_t p = j0; p < xn; p += dj) {
-            int32_t w = g.col[xb + p];
-            int64_t q = nd_find(g.col + yb, yn, w);
-            if (q < 0) continue;
-            int32_t e_xw = g.pos2e[xb + p], e_yw = g.pos2e[yb + q];
-            for (int64_t jx = g.dg_rp[w]; jx < g.dg_rp[w + 1]; ++jx) {
-                int32_t x = g.dg_col[jx];
-                int64_t px = nd_find(g.col + xb, xn, x);
-                if (px < 0) continue;
-                int64_t py = nd_find(g.col + yb, yn, x);
-                if (py < 0) continue;
-                int32_t o[5] = {e_xw, e_yw, g.pos2e[xb + px], g.pos2e[yb + py], g.dg_eid[jx]};
-                update_func<CT, 5>(E, R, o, k);
-            }
-        }
+
+    // the 4-cliques of candidate pair number p (0 <= p < pre[cnt]) of the staged I
+    __device__ static void pair(const GraphView& g, const RoundEnv<CT>& E, int32_t R, const Stage24& st, int cnt,
+                                int32_t p, UpdCounters& k) {
+        int i = stage_owner(st.pre, cnt, p);
+        int64_t jx = (int64_t)st.base[i] + (p - st.pre[i]);
+        int j = stage_find(st.w, cnt, g.dg_col[jx]);
+        if (j < 0) return;
+        int32_t o[5] = {st.ex[i], st.ey[i], st.ex[j], st.ey[j], g.dg_eid[jx]};
+        update_func<CT, 5>(E, R, o, k);
     }
-    // One warp: I (with the edge ids to u and v) staged in shared memory, then every DG edge
-    // w -> x with w, x in I found by a binary search of x in the staged I.
+
+    // One warp; the stage is this warp's shared memory (capacity kI24).
     __device__ static void run_warp(const GraphView& g, const RoundEnv<CT>& E, int32_t R, UpdCounters& k,
-                                    int32_t* sw, int32_t* sx, int32_t* sy) {
+                                    const Stage24& st) {
         int lane = threadIdx.x & 31;
         int32_t u = g.eu[R], v = g.ev[R];
         int64_t ub = g.rp[u], un = g.rp[u + 1] - ub, vb = g.rp[v], vn = g.rp[v + 1] - vb;
@@ -587,48 +614,112 @@ struct Upd24 {
         int64_t xb = u_drives ? ub : vb, xn = u_drives ? un : vn;
         int64_t yb = u_drives ? vb : ub, yn = u_drives ? vn : un;
         int cnt = 0;
-        bool overflow = false;
         for (int64_t p0 = 0; p0 < xn; p0 += 32) {
             int64_t p = p0 + lane;
             int64_t q = -1;
-            if (p < xn) q = nd_find(g.col + yb, yn, g.col[xb + p]);
+            // w joins I only with both edges to R unpeeled before this round: every S through an
+            // edge peeled earlier is dead already
+            if (p < xn && E.P.rnd[g.pos2e[xb + p]] >= E.t) {
+                q = nd_find(g.col + yb, yn, g.col[xb + p]);
+                if (q >= 0 && E.P.rnd[g.pos2e[yb + q]] < E.t) q = -1;
+            }
             unsigned m = __ballot_sync(0xffffffffu, q >= 0);
-            int at = cnt + __popc(m & nd_lanemask_lt());
-            if (q >= 0 && at < kI24) {
-                sw[at] = g.col[xb + p];
-                sx[at] = g.pos2e[xb + p];
-                sy[at] = g.pos2e[yb + q];
+            if (q >= 0) {
+                int at = cnt + __popc(m & nd_lanemask_lt());
+                int32_t w = g.col[xb + p];
+                st.w[at] = w;
+                st.ex[at] = g.pos2e[xb + p];
+                st.ey[at] = g.pos2e[yb + q];
+                st.base[at] = (int32_t)g.dg_rp[w];
+                st.pre[at] = (int32_t)(g.dg_rp[w + 1] - g.dg_rp[w]);
             }
             cnt += __popc(m);
-            if (cnt > kI24) {
-                overflow = true;
-                break;
-            }
         }
         __syncwarp();
-        if (overflow) {
-            run(g, E, R, lane, 32, k);
-            return;
+        // exclusive prefix of the out-degrees (cnt <= kI24 < 128: at most four 32-wide chunks)
+        int32_t carry = 0;
+        for (int c0 = 0; c0 < cnt; c0 += 32) {
+            int i = c0 + lane;
+            int32_t d = i < cnt ? st.pre[i] : 0, inc = d;
+            for (int o = 1; o < 32; o <<= 1) {
+                int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            if (i < cnt) st.pre[i] = carry + inc - d;
+            carry += __shfl_sync(0xffffffffu, inc, 31);
         }
-        for (int i = lane; i < cnt; i += 32) {
-            int32_t w = sw[i];
-            for (int64_t jx = g.dg_rp[w]; jx < g.dg_rp[w + 1]; ++jx) {
-                int32_t x = g.dg_col[jx];
-                // binary search of x in the staged I (ascending)
-                int lo = 0, hi = cnt;
-                while (lo < hi) {
-                    int mid = (lo + hi) >> 1;
-                    if (sw[mid] < x)
-                        lo = mid + 1;
-                    else
-                        hi = mid;
+        if (lane == 0) st.pre[cnt] = carry;
+        __syncwarp();
+        for (int32_t p = lane; p < carry; p += 32) pair(g, E, R, st, cnt, p, k);
+        __syncwarp();
+    }
+
+    // One block (the heavy phase); the stage is the block's global scratch slice. Every thread of
+    // the block calls it.
+    __device__ static void run_block(const GraphView& g, const RoundEnv<CT>& E, int32_t R, UpdCounters& k,
+                                     const Stage24& st) {
+        __shared__ int32_t s_tot[kMaxWarpsPerBlock];
+        __shared__ int32_t s_cnt, s_carry;
+        int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        int32_t u = g.eu[R], v = g.ev[R];
+        int64_t ub = g.rp[u], un = g.rp[u + 1] - ub, vb = g.rp[v], vn = g.rp[v + 1] - vb;
+        bool u_drives = un <= vn;
+        int64_t xb = u_drives ? ub : vb, xn = u_drives ? un : vn;
+        int64_t yb = u_drives ? vb : ub, yn = u_drives ? vn : un;
+        if (threadIdx.x == 0) s_cnt = 0;
+        __syncthreads();
+        // stage I in ascending order: block-wide ordered compaction, blockDim elements at a time
+        for (int64_t p0 = 0; p0 < xn; p0 += blockDim.x) {
+            int64_t p = p0 + threadIdx.x;
+            int64_t q = -1;
+            if (p < xn && E.P.rnd[g.pos2e[xb + p]] >= E.t) {
+                q = nd_find(g.col + yb, yn, g.col[xb + p]);
+                if (q >= 0 && E.P.rnd[g.pos2e[yb + q]] < E.t) q = -1;
+            }
+            unsigned m = __ballot_sync(0xffffffffu, q >= 0);
+            if (lane == 0) s_tot[wid] = __popc(m);
+            __syncthreads();
+            int before = 0, tot = 0;
+            for (int x = 0; x < nw; ++x) {
+                before += x < wid ? s_tot[x] : 0;
+                tot += s_tot[x];
+            }
+            if (q >= 0) {
+                int at = s_cnt + before + __popc(m & nd_lanemask_lt());
+                int32_t w = g.col[xb + p];
+                st.w[at] = w;
+                st.ex[at] = g.pos2e[xb + p];
+                st.ey[at] = g.pos2e[yb + q];
+                st.base[at] = (int32_t)g.dg_rp[w];
+                st.pre[at] = (int32_t)(g.dg_rp[w + 1] - g.dg_rp[w]);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) s_cnt += tot;
+            __syncthreads();
+        }
+        int cnt = s_cnt;
+        // exclusive prefix of the out-degrees (one warp; the totals fit int32: at most m)
+        if (wid == 0) {
+            int32_t carry = 0;
+            for (int c0 = 0; c0 < cnt; c0 += 32) {
+                int i = c0 + lane;
+                int32_t d = i < cnt ? st.pre[i] : 0, inc = d;
+                for (int o = 1; o < 32; o <<= 1) {
+                    int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= o) inc += y;
                 }
-                if (lo >= cnt || sw[lo] != x) continue;
-                int32_t o[5] = {sx[i], sy[i], sx[lo], sy[lo], g.dg_eid[jx]};
-                update_func<CT, 5>(E, R, o, k);
+                if (i < cnt) st.pre[i] = carry + inc - d;
+                carry += __shfl_sync(0xffffffffu, inc, 31);
+            }
+            if (lane == 0) {
+                st.pre[cnt] = carry;
+                s_carry = carry;
             }
         }
-        __syncwarp();
+        __syncthreads();
+        int32_t total = s_carry;
+        for (int32_t p = threadIdx.x; p < total; p += blockDim.x) pair(g, E, R, st, cnt, p, k);
+        __syncthreads();
     }
 };
 
@@ -710,12 +801,21 @@ struct Upd34 {
 };
 
 template <typename U, typename = void>
-struct has_warp_smem {
+struct is_staged {
     static constexpr bool value = false;
 };
 template <typename U>
-struct has_warp_smem<U, decltype((void)U::kWarpSmem)> {
-    static constexpr bool value = U::kWarpSmem;
+struct is_staged<U, decltype((void)U::kStaged)> {
+    static constexpr bool value = U::kStaged;
+};
+
+template <typename U, typename = void>
+struct heavy_work {
+    static constexpr int64_t value = kHeavy;
+};
+template <typename U>
+struct heavy_work<U, decltype((void)U::kHeavyWork)> {
+    static constexpr int64_t value = U::kHeavyWork;
 };
 
 template <typename CT, typename U>
@@ -726,7 +826,7 @@ __device__ void phase_update(const GraphView& g, const PeelView<CT>& P) {
     UpdCounters k;
     for (int64_t i = gwarp(); i < E.nA; i += nwarps()) {
         int32_t R = E.A[i];
-        if (U::work(g, R) > kHeavy) {
+        if (U::work(g, R) > heavy_work<U>::value) {
             int queued = 0;
             if (lane == 0) {
                 unsigned slot = atomicAdd(&P.ctl->nH, 1u);
@@ -736,12 +836,19 @@ __device__ void phase_update(const GraphView& g, const PeelView<CT>& P) {
                 }
             }
             if (__shfl_sync(0xffffffffu, queued, 0)) continue;
+            if constexpr (is_staged<U>::value) {
+                // the staged warp path holds at most kI24 entries; the list is sized to hold
+                // every r-clique for staged functors, so this is unreachable
+                if (lane == 0) atomicOr(&P.ctl->err, 1);
+                continue;
+            }
         }
-        if constexpr (has_warp_smem<U>::value) {
+        if constexpr (is_staged<U>::value) {
             __shared__ int32_t s_w[kMaxWarpsPerBlock][kI24], s_x[kMaxWarpsPerBlock][kI24],
-                s_y[kMaxWarpsPerBlock][kI24];
+                s_y[kMaxWarpsPerBlock][kI24], s_b[kMaxWarpsPerBlock][kI24], s_p[kMaxWarpsPerBlock][kI24 + 1];
             int wid = threadIdx.x >> 5;
-            U::run_warp(g, E, R, k, s_w[wid], s_x[wid], s_y[wid]);
+            Stage24 stg{s_w[wid], s_x[wid], s_y[wid], s_b[wid], s_p[wid]};
+            U::run_warp(g, E, R, k, stg);
         } else {
             U::run(g, E, R, lane, 32, k);
         }
@@ -758,7 +865,18 @@ __device__ void phase_update_heavy(const GraphView& g, const PeelView<CT>& P) {
     UpdCounters k;
     // one block per heavy r-clique, its threads striding the driving list: heavy r-cliques run
     // side by side, each over many threads
-    for (unsigned h = blockIdx.x; h < nH; h += gridDim.x) U::run(g, E, P.H[h], threadIdx.x, blockDim.x, k);
+    if constexpr (is_staged<U>::value) {
+        // blocks below hslices own a scratch slice of 5 * (hstage + 1) int32 and share the list
+        unsigned ns = (unsigned)P.hslices < gridDim.x ? (unsigned)P.hslices : gridDim.x;
+        if (blockIdx.x < ns) {
+            int64_t c = P.hstage + 1;
+            int32_t* base = P.hscratch + (int64_t)blockIdx.x * 5 * c;
+            Stage24 stg{base, base + c, base + 2 * c, base + 3 * c, base + 4 * c};
+            for (unsigned h = blockIdx.x; h < nH; h += ns) U::run_block(g, E, P.H[h], k, stg);
+        }
+    } else {
+        for (unsigned h = blockIdx.x; h < nH; h += gridDim.x) U::run(g, E, P.H[h], threadIdx.x, blockDim.x, k);
+    }
     add_counters(P.ctl, k);
 }
 
@@ -917,6 +1035,8 @@ cudaError_t launch_peel_loop(const GraphView& g, const PeelView<CT>& P, cudaStre
 int peel_blocks() { return nd_sm_count() * 4; }
 
 }  // namespace
+
+int nd_peel_heavy_slices() { return nd_sm_count() * 2; }
 
 void nd_peel_init(PeelCtl* ctl, int64_t n_r, int64_t max_rounds, cudaStream_t st) {
     ND_K(k_init<<<1, 32, 0, st>>>(ctl, n_r, max_rounds));
