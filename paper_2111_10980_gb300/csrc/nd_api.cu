@@ -595,6 +595,35 @@ extern "C" int nd_count(nd_graph* g, int r, int s, int count_width, void* counts
 // ------------------------------------------------------------------------------------
 // peeling
 
+// Hash directory of the triangle lists for the (3,4) Update: table offsets per edge (an exclusive
+// scan of the per-list slot counts) and the tables, filled from the index.
+static int build_tri_hash(nd_graph* g, DBuf& hoff, DBuf& htab) {
+    nd_ctx* c = g->ctx;
+    cudaStream_t st = c->stream;
+    int64_t m = g->m;
+    DBuf slots, tmp;
+    int rc = ND_OK;
+    if ((rc = nd_alloc(c, slots, sizeof(int64_t) * std::max<int64_t>(m, 1))) ||
+        (rc = nd_alloc(c, tmp, nd_scan_tmp_bytes(m))) || (rc = nd_alloc(c, hoff, sizeof(int64_t) * (m + 1)))) {
+        nd_free(c, slots);
+        nd_free(c, tmp);
+        return rc;
+    }
+    GraphView v = nd_view(g);
+    nd_tri_hash_sizes(v, (int64_t*)slots.p, st);
+    nd_scan_i64((const int64_t*)slots.p, (int64_t*)hoff.p, m, tmp.p, st);
+    int64_t total = 0;
+    rc = nd_check_launch("triangle hash");
+    if (!rc) rc = read_back(g, (int64_t*)hoff.p + m, &total, "triangle hash");
+    nd_free(c, slots);
+    nd_free(c, tmp);
+    if (!rc) rc = nd_alloc(c, htab, sizeof(unsigned long long) * std::max<int64_t>(total, 1));
+    if (rc) return rc;
+    ND_CUDA(cudaMemsetAsync(htab.p, 0xff, htab.bytes, st));
+    nd_tri_hash_fill(v, (const int64_t*)hoff.p, (unsigned long long*)htab.p, st);
+    return nd_check_launch("triangle hash");
+}
+
 template <typename CT>
 static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags, PeelOut& po) {
     nd_ctx* c = g->ctx;
@@ -619,13 +648,14 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
         hstage = g->edge_mindeg;
         hslices = nd_peel_heavy_slices();
     }
-    DBuf ctl, A0, A1, N0, N1, L0, L1, H, rs, rl, etr, hsc;
+    DBuf ctl, A0, A1, N0, N1, L0, L1, H, rs, rl, etr, hsc, abits, hoff, htab;
     if ((rc = nd_alloc(c, ctl, sizeof(PeelCtl))) || (rc = nd_alloc(c, A0, 4 * cap)) || (rc = nd_alloc(c, A1, 4 * cap)) ||
         (rc = nd_alloc(c, N0, 4 * cap)) || (rc = nd_alloc(c, N1, 4 * cap)) || (rc = nd_alloc(c, L0, 4 * cap)) ||
         (rc = nd_alloc(c, L1, 4 * cap)) || (rc = nd_alloc(c, H, 4 * hcap)) || (rc = nd_alloc(c, rs, 8 * rcap)) ||
         (rc = nd_alloc(c, rl, 8 * rcap)) || (r == 3 && (rc = nd_alloc(c, etr, 4 * std::max<int64_t>(3 * g->n3, 1)))) ||
-        (staged && (rc = nd_alloc(c, hsc, 4 * 5 * (hstage + 1) * hslices)))) {
-        for (DBuf* b : {&ctl, &A0, &A1, &N0, &N1, &L0, &L1, &H, &rs, &rl, &etr, &hsc}) nd_free(c, *b);
+        (staged && (rc = nd_alloc(c, hsc, 4 * 5 * (hstage + 1) * hslices))) ||
+        (rc = nd_alloc(c, abits, 4 * ((cap + 31) / 32)))) {
+        for (DBuf* b : {&ctl, &A0, &A1, &N0, &N1, &L0, &L1, &H, &rs, &rl, &etr, &hsc, &abits, &hoff, &htab}) nd_free(c, *b);
         return rc;
     }
     PeelView<CT> P;
@@ -643,6 +673,11 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
     P.hscratch = (int32_t*)hsc.p;
     P.hstage = hstage;
     P.hslices = (int32_t)hslices;
+    P.abits = (uint32_t*)abits.p;
+    // a round sorts A when it holds at least 1/8192 of the r-cliques (and 2048): then the two
+    // passes over the bitmap cost little next to the Update they make cache-friendly
+    P.sort_min = (uint32_t)std::max<int64_t>(n_r / 8192, 2048);
+    cudaMemsetAsync(abits.p, 0, abits.bytes, st);  // a failure surfaces at the launch check below
     P.cap = (uint32_t)cap;
     P.ctl = (PeelCtl*)ctl.p;
     P.round_size = (int64_t*)rs.p;
@@ -652,7 +687,16 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
     P.tri_e = nullptr;
     P.tri_pos = nullptr;
     P.et_rp = nullptr;
+    P.hoff = nullptr;
+    P.htab = nullptr;
+    if (r == 3 && (rc = build_tri_hash(g, hoff, htab))) {
+        for (DBuf* b : {&ctl, &A0, &A1, &N0, &N1, &L0, &L1, &H, &rs, &rl, &etr, &hsc, &abits, &hoff, &htab})
+            nd_free(c, *b);
+        return rc;
+    }
     if (r == 3) {
+        P.hoff = (const int64_t*)hoff.p;
+        P.htab = (const unsigned long long*)htab.p;
         P.et_rnd = (int32_t*)etr.p;
         P.tri_e = (const int32_t*)g->tri_e.p;
         P.tri_pos = (const int32_t*)g->tri_pos.p;
@@ -778,7 +822,7 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
             rc = nd_sync(c, "peel record");
         }
     }
-    for (DBuf* b : {&ctl, &A0, &A1, &N0, &N1, &L0, &L1, &H, &rs, &rl, &etr, &hsc}) nd_free(c, *b);
+    for (DBuf* b : {&ctl, &A0, &A1, &N0, &N1, &L0, &L1, &H, &rs, &rl, &etr, &hsc, &abits, &hoff, &htab}) nd_free(c, *b);
     return rc;
 }
 

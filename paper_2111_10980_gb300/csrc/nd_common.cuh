@@ -111,6 +111,36 @@ __device__ __forceinline__ void nd_warp_merge(const int32_t* __restrict__ A, int
     }
 }
 
+// Hash directory of the triangle lists (built for a (3,4) peel): list L(e) with more than
+// ND_HASH_MIN entries gets an open-addressing table of 2^k >= 2 |L(e)| slots (load <= 1/2),
+// linear probing; a slot holds (vertex w << 32) | triangle id, ND_HASH_EMPTY when free.
+#define ND_HASH_MIN 32
+#define ND_HASH_EMPTY 0xffffffffffffffffull
+
+__host__ __device__ __forceinline__ bool nd_hashed(int64_t n) { return n > ND_HASH_MIN && n <= ((int64_t)1 << 30); }
+
+__host__ __device__ __forceinline__ int nd_hash_bits(int64_t n) {
+    int k = 0;
+    while (((int64_t)1 << k) < 2 * n) ++k;
+    return k;
+}
+
+__device__ __forceinline__ uint32_t nd_hash_slot(int32_t w, int k) {
+    return ((uint32_t)w * 0x9E3779B1u) >> (32 - k);  // multiplicative hashing (Knuth), top k bits
+}
+
+// triangle id stored for w in the table of 2^k slots, or -1
+__device__ __forceinline__ int32_t nd_hash_find(const unsigned long long* __restrict__ tab, int k, int32_t w) {
+    uint32_t mask = (1u << k) - 1u, s = nd_hash_slot(w, k);
+    for (uint32_t probes = 0; probes <= mask; ++probes) {
+        unsigned long long v = __ldg(tab + s);
+        if (v == ND_HASH_EMPTY) return -1;
+        if ((int32_t)(v >> 32) == w) return (int32_t)(v & 0xffffffffu);
+        s = (s + 1) & mask;
+    }
+    return -1;
+}
+
 // Use the warp merge when the longer list is at most this many times the shorter one (plus a
 // constant), else per-lane binary searches of the shorter list's elements in the longer one.
 __device__ __forceinline__ bool nd_prefer_merge(int64_t n_short, int64_t n_long) {
@@ -166,7 +196,9 @@ struct PeelCtl {
     int32_t started;    // 0 before the first round
     int32_t wa, wn, wl; // ping-pong selectors of the A, N and L lists
     int32_t lmat;       // 0: L is implicitly 0..n_r-1
-    int32_t pad0;
+    int32_t heavy;      // persistent kernel: this round has a heavy phase (set by a serial step)
+    int32_t sorta;      // persistent kernel: this round rebuilds A in id order (set by a serial step)
+    int32_t pad1;
     int64_t k;          // current level
     int64_t hi;         // bucket window: N holds every unpeeled r-clique with count < hi
     int64_t finished;   // r-cliques peeled so far
@@ -208,6 +240,12 @@ struct PeelView {
     int32_t* hscratch;
     int64_t hstage;
     int32_t hslices;
+    // membership bitmap of A (NULL: never sorted) and the |A| from which a round sorts A
+    uint32_t* abits;
+    uint32_t sort_min;
+    // (3,4): hash directory of the triangle lists (table offset per edge, tables), or NULL
+    const int64_t* hoff;
+    const unsigned long long* htab;
     // (3,4) only: the round tag of every triangle-index entry, and what is needed to find the
     // three entries of a triangle (NULL for other (r,s))
     int32_t* et_rnd;
@@ -264,6 +302,9 @@ void nd_edge_fill_tid(const GraphView& g, int32_t* et_t, int32_t* tri_pos, cudaS
 void nd_tri_tuples(const GraphView& g, int32_t* out, cudaStream_t st);
 void nd_edge_tuples(const GraphView& g, int32_t* out, cudaStream_t st);
 void nd_max_edge_mindeg(const GraphView& g, unsigned long long* out, cudaStream_t st);
+// hash directory of the triangle lists: slots per edge (0 for short lists), then the tables
+void nd_tri_hash_sizes(const GraphView& g, int64_t* slots, cudaStream_t st);
+void nd_tri_hash_fill(const GraphView& g, const int64_t* hoff, unsigned long long* tab, cudaStream_t st);
 // blocks of the (2,4) heavy phase that hold a scratch slice; the others skip the phase
 int nd_peel_heavy_slices();
 

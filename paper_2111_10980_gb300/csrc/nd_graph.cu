@@ -293,7 +293,46 @@ __global__ void k_max_edge_mindeg(GraphView g, unsigned long long* __restrict__ 
     if ((threadIdx.x & 31) == 0 && best) atomicMax(out, best);
 }
 
+__global__ void k_tri_hash_sizes(GraphView g, int64_t* __restrict__ slots) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < g.m; e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t n = g.et_rp[e + 1] - g.et_rp[e];
+        slots[e] = nd_hashed(n) ? ((int64_t)1 << nd_hash_bits(n)) : 0;
+    }
+}
+
+// one warp per long list; each entry claims a free slot by compare-and-swap
+__global__ void k_tri_hash_fill(GraphView g, const int64_t* __restrict__ hoff, unsigned long long* __restrict__ tab) {
+    int lane = threadIdx.x & 31;
+    for (int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < g.m;
+         e += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        int64_t b = g.et_rp[e], n = g.et_rp[e + 1] - b;
+        if (!nd_hashed(n)) continue;
+        int k = nd_hash_bits(n);
+        uint32_t mask = (1u << k) - 1u;
+        unsigned long long* t = tab + hoff[e];
+        for (int64_t p = lane; p < n; p += 32) {
+            int32_t w = g.et_w[b + p];
+            unsigned long long v = ((unsigned long long)(uint32_t)w << 32) | (uint32_t)g.et_t[b + p];
+            uint32_t s = nd_hash_slot(w, k);
+            for (uint32_t probes = 0; probes <= mask; ++probes) {
+                if (atomicCAS(t + s, ND_HASH_EMPTY, v) == ND_HASH_EMPTY) break;
+                s = (s + 1) & mask;
+            }
+        }
+    }
+}
+
 }  // namespace
+
+void nd_tri_hash_sizes(const GraphView& g, int64_t* slots, cudaStream_t st) {
+    if (g.m <= 0) return;
+    ND_K(k_tri_hash_sizes<<<blocks_for_threads(g.m), kThreads, 0, st>>>(g, slots));
+}
+
+void nd_tri_hash_fill(const GraphView& g, const int64_t* hoff, unsigned long long* tab, cudaStream_t st) {
+    if (g.m <= 0) return;
+    ND_K(k_tri_hash_fill<<<blocks_for_warps(g.m), kThreads, 0, st>>>(g, hoff, tab));
+}
 
 void nd_max_edge_mindeg(const GraphView& g, unsigned long long* out, cudaStream_t st) {
     if (g.m <= 0) return;

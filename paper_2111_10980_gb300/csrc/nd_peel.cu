@@ -65,6 +65,18 @@ __device__ __forceinline__ void set_tri_round(const PeelView<CT>& P, int64_t R, 
     }
 }
 
+// Membership bitmap of the next / current A (bit x set while x is scheduled and not yet updated):
+// large rounds rebuild A from it in ascending id order, so that warps running side by side work
+// on triangles (edges) that share lists and the lists' lines are reused from L2.
+template <typename CT>
+__device__ __forceinline__ void mark_a(const PeelView<CT>& P, int32_t x) {
+    if (P.abits) atomicOr(&P.abits[x >> 5], 1u << (x & 31));
+}
+template <typename CT>
+__device__ __forceinline__ void unmark_a(const PeelView<CT>& P, int32_t x) {
+    if (P.abits) atomicAnd(&P.abits[x >> 5], ~(1u << (x & 31)));
+}
+
 // list sizes read back from the control block never exceed the list capacity (an overflow sets
 // ctl->err and is reported by the host)
 __device__ __forceinline__ unsigned clampn(unsigned v, uint32_t cap) { return v < cap ? v : cap; }
@@ -101,6 +113,8 @@ __global__ void k_init(PeelCtl* c, int64_t n_r, int64_t max_rounds) {
         c->started = 0;
         c->wa = c->wn = c->wl = 0;
         c->lmat = 0;
+        c->heavy = 0;
+        c->sorta = 0;
         c->k = 0;
         c->hi = 0;
         c->finished = 0;
@@ -362,6 +376,7 @@ __device__ void phase_adv_select(const PeelView<CT>& P) {
                     P.rnd[R] = t;
                     P.core[R] = (int32_t)kn;
                     if (P.et_rnd) set_tri_round(P, R, t);
+                    mark_a(P, R);
                     nd_append(&c->cntA, A, P.cap, R, &c->err);
                 } else {
                     nd_append(&c->nN2, N2, P.cap, R, &c->err);
@@ -381,6 +396,84 @@ template <typename CT>
 __global__ void k_refill_select(PeelView<CT> P) { phase_refill_select(P); }
 template <typename CT>
 __global__ void k_adv_select(PeelView<CT> P) { phase_adv_select(P); }
+
+// Rebuild A in ascending id order from the membership bitmap (persistent kernel, large rounds):
+// each block owns a fixed range of bitmap words; pass 1 counts its members, the serial step of the
+// barrier turns the per-block counts (hist[0 .. gridDim)) into offsets, pass 2 writes the ids.
+__device__ __forceinline__ void sort_range(const PeelCtl* c, int64_t& w0, int64_t& w1) {
+    int64_t nwords = (c->n_r + 31) >> 5;
+    int64_t per = (nwords + gridDim.x - 1) / gridDim.x;
+    w0 = (int64_t)blockIdx.x * per;
+    w1 = w0 + per < nwords ? w0 + per : nwords;
+    if (w0 > w1) w0 = w1;
+}
+
+// exclusive prefix over the block (every thread calls it); returns the block total
+__device__ unsigned block_excl_sum(unsigned v, unsigned& excl) {
+    __shared__ unsigned s_warp[32];
+    __shared__ unsigned s_total;
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    unsigned inc = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_warp[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        unsigned x = lane < nw ? s_warp[lane] : 0, xi = x;
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned y = __shfl_up_sync(0xffffffffu, xi, o);
+            if (lane >= o) xi += y;
+        }
+        if (lane < nw) s_warp[lane] = xi - x;
+        if (lane == 31) s_total = xi;
+    }
+    __syncthreads();
+    excl = s_warp[wid] + inc - v;
+    unsigned total = s_total;
+    __syncthreads();
+    return total;
+}
+
+template <typename CT>
+__device__ void phase_sort_count(const PeelView<CT>& P) {
+    PeelCtl* c = P.ctl;
+    int64_t w0, w1;
+    sort_range(c, w0, w1);
+    unsigned cnt = 0, excl;
+    for (int64_t w = w0 + threadIdx.x; w < w1; w += blockDim.x) cnt += __popc(P.abits[w]);
+    unsigned total = block_excl_sum(cnt, excl);
+    if (threadIdx.x == 0) c->hist[blockIdx.x] = total;
+}
+
+template <typename CT>
+__device__ void phase_sort_write(const PeelView<CT>& P) {
+    PeelCtl* c = P.ctl;
+    int64_t w0, w1;
+    sort_range(c, w0, w1);
+    int32_t* A = pick(P.A, c->wa);
+    unsigned long long at = c->hist[blockIdx.x];
+    for (int64_t base = w0; base < w1; base += blockDim.x) {
+        int64_t w = base + threadIdx.x;
+        uint32_t bits = w < w1 ? P.abits[w] : 0u;
+        unsigned excl;
+        unsigned total = block_excl_sum(__popc(bits), excl);
+        unsigned long long o = at + excl;
+        while (bits) {
+            int b = __ffs(bits) - 1;
+            bits &= bits - 1;
+            if (o < P.cap) A[o] = (int32_t)(w * 32 + b);
+            ++o;
+        }
+        at += total;
+    }
+}
+
+template <typename CT>
+__global__ void k_sort_count(PeelView<CT> P) { phase_sort_count(P); }
+template <typename CT>
+__global__ void k_sort_write(PeelView<CT> P) { phase_sort_write(P); }
 
 // ------------------------------------------------------------------------------------
 // Update
@@ -429,6 +522,7 @@ __device__ __forceinline__ void after_dec(const RoundEnv<CT>& E, int32_t x, int6
         E.P.rnd[x] = E.t + 1;
         E.P.core[x] = (int32_t)E.k;
         if (E.P.et_rnd) set_tri_round(E.P, x, E.t + 1);
+        mark_a(E.P, x);
         nd_append(&E.P.ctl->nNext, E.next, E.P.cap, x, &E.P.ctl->err);
     }
     if (o >= E.hi && o - 1 < E.hi) nd_append(E.ncnt, E.Ncur, E.P.cap, x, &E.P.ctl->err);
@@ -477,45 +571,65 @@ __device__ __forceinline__ void add_counters(PeelCtl* c, UpdCounters k) {
 //   run(g, E, R, j0, dj, lst):  lists the s-cliques containing R from driver entries
 //                               j0, j0 + dj, ... (lanes of one warp: j0 = lane, dj = 32;
 //                               the whole grid on one heavy R: j0 = global lane, dj = all lanes).
-// The light kernel gives each warp one R at a time and defers R with work > kHeavy to a list that
-// the heavy kernel then gives one block each (threads striding the driving list), so a few hub
-// r-cliques in a round do not serialise on single warps.
+// Work of one r-clique R: the driving list (b[0], n[0]) whose entries are the candidates, and the
+// lists they are searched in. prep() fills it and returns n[0]; cand() handles candidate j; run()
+// is threads j0, j0 + dj, ... over all candidates of one R.
+struct Prep {
+    int64_t b[3];
+    int64_t n[3];
+    int64_t h[3];  // (3,4): hash-table offset of the list, -1 when it is searched by bisection
+};
+
+// The light Update phase gives each warp one R at a time (its lanes share the R's lists, so the
+// upper levels of their searches hit the same lines) and defers R with work > kHeavy to a list
+// that the heavy phase gives one block each, so a few hub r-cliques in a round do not serialise
+// on single warps.
 constexpr int64_t kHeavy = 4096;
+
+template <typename U, typename CT>
+__device__ __forceinline__ void run_all(const GraphView& g, const RoundEnv<CT>& E, int32_t R, int64_t j0,
+                                        int64_t dj, UpdCounters& k) {
+    Prep q;
+    int64_t n0 = U::prep(g, E.P, R, q);
+    for (int64_t j = j0; j < n0; j += dj) U::cand(g, E, R, q, j, k);
+}
 
 // (1,2): R = v; S = {v, w} for every neighbour w.
 template <typename CT>
 struct Upd12 {
-    __device__ static int64_t work(const GraphView& g, int32_t v) { return g.rp[v + 1] - g.rp[v]; }
-    __device__ static void run(const GraphView& g, const RoundEnv<CT>& E, int32_t v, int64_t j0, int64_t dj,
-                               UpdCounters& k) {
-        int64_t b = g.rp[v], e = g.rp[v + 1];
-        for (int64_t p = b + j0; p < e; p += dj) {
-            int32_t o[1] = {g.col[p]};
-            update_func<CT, 1>(E, v, o, k);
-        }
+    __device__ static int64_t prep(const GraphView& g, const PeelView<CT>&, int32_t v, Prep& q) {
+        q.b[0] = g.rp[v];
+        q.n[0] = g.rp[v + 1] - q.b[0];
+        return q.n[0];
+    }
+    __device__ static void cand(const GraphView& g, const RoundEnv<CT>& E, int32_t v, const Prep& q, int64_t j,
+                                UpdCounters& k) {
+        int32_t o[1] = {g.col[q.b[0] + j]};
+        update_func<CT, 1>(E, v, o, k);
     }
 };
 
 // (1,3): R = v; S = {v, w, x} for every edge w -> x of DG inside N(v).
 template <typename CT>
 struct Upd13 {
-    __device__ static int64_t work(const GraphView& g, int32_t v) { return g.rp[v + 1] - g.rp[v]; }
-    __device__ static void run(const GraphView& g, const RoundEnv<CT>& E, int32_t v, int64_t j0, int64_t dj,
-                               UpdCounters& k) {
-        int64_t b = g.rp[v], e = g.rp[v + 1];
-        for (int64_t p = b + j0; p < e; p += dj) {
-            int32_t w = g.col[p];
-            for (int64_t jx = g.dg_rp[w]; jx < g.dg_rp[w + 1]; ++jx) {
-                int32_t x = g.dg_col[jx];
-                if (nd_find(g.col + b, e - b, x) < 0) continue;
-                int32_t o[2] = {w, x};
-                update_func<CT, 2>(E, v, o, k);
-            }
+    __device__ static int64_t prep(const GraphView& g, const PeelView<CT>&, int32_t v, Prep& q) {
+        q.b[0] = g.rp[v];
+        q.n[0] = g.rp[v + 1] - q.b[0];
+        return q.n[0];
+    }
+    __device__ static void cand(const GraphView& g, const RoundEnv<CT>& E, int32_t v, const Prep& q, int64_t j,
+                                UpdCounters& k) {
+        int32_t w = g.col[q.b[0] + j];
+        for (int64_t jx = g.dg_rp[w]; jx < g.dg_rp[w + 1]; ++jx) {
+            int32_t x = g.dg_col[jx];
+            if (nd_find(g.col + q.b[0], q.n[0], x) < 0) continue;
+            int32_t o[2] = {w, x};
+            update_func<CT, 2>(E, v, o, k);
         }
     }
 };
 
-// (2,3): R = (u,v); S = {u, v, w} for w in N(u) ∩ N(v).
+// (2,3): R = (u,v); S = {u, v, w} for w in N(u) ∩ N(v); the shorter row drives.
 template <typename CT>
 struct Upd23 {
     __device__ static int64_t work(const GraphView& g, int32_t R) {
@@ -523,24 +637,26 @@ struct Upd23 {
         int64_t du = g.rp[u + 1] - g.rp[u], dv = g.rp[v + 1] - g.rp[v];
         return du < dv ? du : dv;
     }
-    __device__ static void run(const GraphView& g, const RoundEnv<CT>& E, int32_t R, int64_t j0, int64_t dj,
-                               UpdCounters& k) {
+    __device__ static int64_t prep(const GraphView& g, const PeelView<CT>&, int32_t R, Prep& q) {
         int32_t u = g.eu[R], v = g.ev[R];
-        int64_t xb = g.rp[u], xe = g.rp[u + 1], yb = g.rp[v], ye = g.rp[v + 1];
-        if (xe - xb > ye - yb) {
-            int64_t t0 = xb, t1 = xe;
-            xb = yb, xe = ye, yb = t0, ye = t1;
-        }
-        for (int64_t p = xb + j0; p < xe; p += dj) {
-            // the edge to the candidate, peeled in an earlier round: every S through it is dead
-            int32_t e_xw = g.pos2e[p];
-            if (E.P.rnd[e_xw] < E.t) continue;
-            int32_t w = g.col[p];
-            int64_t q = nd_find(g.col + yb, ye - yb, w);
-            if (q < 0) continue;
-            int32_t o[2] = {e_xw, g.pos2e[yb + q]};
-            update_func<CT, 2>(E, R, o, k);
-        }
+        int64_t ub = g.rp[u], un = g.rp[u + 1] - ub, vb = g.rp[v], vn = g.rp[v + 1] - vb;
+        bool u_drives = un <= vn;
+        q.b[0] = u_drives ? ub : vb;
+        q.n[0] = u_drives ? un : vn;
+        q.b[1] = u_drives ? vb : ub;
+        q.n[1] = u_drives ? vn : un;
+        return q.n[0];
+    }
+    __device__ static void cand(const GraphView& g, const RoundEnv<CT>& E, int32_t R, const Prep& q, int64_t j,
+                                UpdCounters& k) {
+        // the edge to the candidate, peeled in an earlier round: every S through it is dead
+        int64_t p = q.b[0] + j;
+        int32_t e_xw = g.pos2e[p];
+        if (E.P.rnd[e_xw] < E.t) return;
+        int64_t r = nd_find(g.col + q.b[1], q.n[1], g.col[p]);
+        if (r < 0) return;
+        int32_t o[2] = {e_xw, g.pos2e[q.b[1] + r]};
+        update_func<CT, 2>(E, R, o, k);
     }
 };
 
@@ -729,50 +845,60 @@ struct Upd24 {
 // tag below the current round means that triangle was peeled earlier, so every S through it is
 // dead and the candidate is dropped before any further search; a tag equal to the round marks a
 // member of A for the owner rule. No per-triangle state is read at random.
-__device__ __forceinline__ void lists34(const GraphView& g, int32_t R, int64_t (&b)[3], int64_t (&n)[3]) {
+template <typename CT>
+__device__ __forceinline__ void lists34(const GraphView& g, const PeelView<CT>& P, int32_t R, Prep& q) {
 #pragma unroll
     for (int x = 0; x < 3; ++x) {
         int32_t e = g.tri_e[3 * (int64_t)R + x];
-        b[x] = g.et_rp[e];
-        n[x] = g.et_rp[e + 1] - b[x];
+        q.b[x] = g.et_rp[e];
+        q.n[x] = g.et_rp[e + 1] - q.b[x];
+        q.h[x] = P.htab && nd_hashed(q.n[x]) ? P.hoff[e] : -1;
     }
     // sort the three lists by length
-    if (n[1] < n[0]) {
-        int64_t tb = b[0], tn = n[0];
-        b[0] = b[1], n[0] = n[1], b[1] = tb, n[1] = tn;
-    }
-    if (n[2] < n[0]) {
-        int64_t tb = b[0], tn = n[0];
-        b[0] = b[2], n[0] = n[2], b[2] = tb, n[2] = tn;
-    }
-    if (n[2] < n[1]) {
-        int64_t tb = b[1], tn = n[1];
-        b[1] = b[2], n[1] = n[2], b[2] = tb, n[2] = tn;
+#pragma unroll
+    for (int pass = 0; pass < 3; ++pass) {
+        int i = pass == 2 ? 1 : 0, j = pass == 0 ? 1 : 2;  // compare-exchange (0,1), (0,2), (1,2)
+        if (q.n[j] < q.n[i]) {
+            int64_t tb = q.b[i], tn = q.n[i], th = q.h[i];
+            q.b[i] = q.b[j], q.n[i] = q.n[j], q.h[i] = q.h[j];
+            q.b[j] = tb, q.n[j] = tn, q.h[j] = th;
+        }
     }
 }
 
 template <typename CT>
 struct Upd34 {
-    __device__ static int64_t work(const GraphView& g, int32_t R) {
-        int64_t b[3], n[3];
-        lists34(g, R, b, n);
-        return n[0];
+    __device__ static int64_t prep(const GraphView& g, const PeelView<CT>& P, int32_t R, Prep& q) {
+        lists34(g, P, R, q);
+        return q.n[0];
     }
-    // S = R + w, with w at position i0 of list 0 and i1 of list 1 (both tags alive or in A).
-    // Only the owner (smallest id of S's members in A) applies S, so as soon as a member in A
-    // with a smaller id than R is known, R stops: the owner does the full check itself.
-    __device__ static void finish(const GraphView& g, const RoundEnv<CT>& E, int32_t R, const int64_t (&b)[3],
-                                  const int64_t (&n)[3], int64_t i0, int64_t i1, int32_t r0, int32_t r1,
-                                  UpdCounters& k) {
-        const int32_t* tag = E.P.et_rnd;
-        int32_t id0 = g.et_t[b[0] + i0], id1 = g.et_t[b[1] + i1];
-        if ((r0 == E.t && id0 < R) || (r1 == E.t && id1 < R)) return;
-        int64_t q2 = nd_find(g.et_w + b[2], n[2], g.et_w[b[0] + i0]);
-        if (q2 < 0) return;
-        int32_t r2 = tag[b[2] + q2];
-        if (r2 < E.t) return;
-        int32_t id2 = g.et_t[b[2] + q2];
-        if (r2 == E.t && id2 < R) return;
+    // the triangle R + w of list x (w's entry in L(e_x)) and its round; false when w is not there
+    __device__ static bool look(const GraphView& g, const RoundEnv<CT>& E, const Prep& q, int x, int32_t w,
+                                int32_t& id, int32_t& r) {
+        if (q.h[x] >= 0) {
+            id = nd_hash_find(E.P.htab + q.h[x], nd_hash_bits(q.n[x]), w);
+            if (id < 0) return false;
+            r = E.P.rnd[id];
+        } else {
+            int64_t i = nd_find(g.et_w + q.b[x], q.n[x], w);
+            if (i < 0) return false;
+            r = E.P.et_rnd[q.b[x] + i];
+            id = g.et_t[q.b[x] + i];
+        }
+        return true;
+    }
+    // S = R + w, w = entry j of list 0. Only the owner (smallest id of S's members in A) applies
+    // S, so R stops as soon as a member in A with a smaller id is known: first the entry's own
+    // triangle (read along the list), then the ones found in lists 1 and 2.
+    __device__ static void cand(const GraphView& g, const RoundEnv<CT>& E, int32_t R, const Prep& q, int64_t j,
+                                UpdCounters& k) {
+        int32_t r0 = E.P.et_rnd[q.b[0] + j];
+        if (r0 < E.t) return;
+        int32_t id0 = g.et_t[q.b[0] + j];
+        if (r0 == E.t && id0 < R) return;
+        int32_t w = g.et_w[q.b[0] + j], id1, r1, id2, r2;
+        if (!look(g, E, q, 1, w, id1, r1) || r1 < E.t || (r1 == E.t && id1 < R)) return;
+        if (!look(g, E, q, 2, w, id2, r2) || r2 < E.t || (r2 == E.t && id2 < R)) return;
         k.listed++;
         // issue the decrements before looking at any result (the atomics overlap in flight)
         int64_t o0 = r0 != E.t ? nd_atomic_dec(&E.P.cnt[id0]) : 0;
@@ -782,21 +908,6 @@ struct Upd34 {
         if (r0 != E.t) after_dec(E, id0, o0);
         if (r1 != E.t) after_dec(E, id1, o1);
         if (r2 != E.t) after_dec(E, id2, o2);
-    }
-    __device__ static void run(const GraphView& g, const RoundEnv<CT>& E, int32_t R, int64_t j0, int64_t dj,
-                               UpdCounters& k) {
-        const int32_t* tag = E.P.et_rnd;
-        int64_t b[3], n[3];
-        lists34(g, R, b, n);
-        for (int64_t j = j0; j < n[0]; j += dj) {
-            int32_t r0 = tag[b[0] + j];
-            if (r0 < E.t) continue;
-            int64_t q1 = nd_find(g.et_w + b[1], n[1], g.et_w[b[0] + j]);
-            if (q1 < 0) continue;
-            int32_t r1 = tag[b[1] + q1];
-            if (r1 < E.t) continue;
-            finish(g, E, R, b, n, j, q1, r0, r1, k);
-        }
     }
 };
 
@@ -822,35 +933,53 @@ template <typename CT, typename U>
 __device__ void phase_update(const GraphView& g, const PeelView<CT>& P) {
     if (P.ctl->done) return;
     RoundEnv<CT> E = round_env(P);
-    int lane = threadIdx.x & 31;
+    const unsigned full = 0xffffffffu;
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     UpdCounters k;
-    for (int64_t i = gwarp(); i < E.nA; i += nwarps()) {
-        int32_t R = E.A[i];
-        if (U::work(g, R) > heavy_work<U>::value) {
-            int queued = 0;
-            if (lane == 0) {
-                unsigned slot = atomicAdd(&P.ctl->nH, 1u);
-                if (slot < P.hcap) {
-                    P.H[slot] = R;
-                    queued = 1;
+    if constexpr (is_staged<U>::value) {
+        // one warp per r-clique, I staged in the warp's shared memory
+        __shared__ int32_t s_w[kMaxWarpsPerBlock][kI24], s_x[kMaxWarpsPerBlock][kI24],
+            s_y[kMaxWarpsPerBlock][kI24], s_b[kMaxWarpsPerBlock][kI24], s_p[kMaxWarpsPerBlock][kI24 + 1];
+        for (int64_t i = gwarp(); i < E.nA; i += nwarps()) {
+            int32_t R = E.A[i];
+            if (lane == 0) unmark_a(P, R);
+            if (U::work(g, R) > heavy_work<U>::value) {
+                int queued = 0;
+                if (lane == 0) {
+                    unsigned slot = atomicAdd(&P.ctl->nH, 1u);
+                    if (slot < P.hcap) {
+                        P.H[slot] = R;
+                        queued = 1;
+                    }
                 }
-            }
-            if (__shfl_sync(0xffffffffu, queued, 0)) continue;
-            if constexpr (is_staged<U>::value) {
-                // the staged warp path holds at most kI24 entries; the list is sized to hold
-                // every r-clique for staged functors, so this is unreachable
+                if (__shfl_sync(full, queued, 0)) continue;
+                // the staged warp path holds at most kI24 entries; the list is sized to hold every
+                // r-clique for staged functors, so this is unreachable
                 if (lane == 0) atomicOr(&P.ctl->err, 1);
                 continue;
             }
-        }
-        if constexpr (is_staged<U>::value) {
-            __shared__ int32_t s_w[kMaxWarpsPerBlock][kI24], s_x[kMaxWarpsPerBlock][kI24],
-                s_y[kMaxWarpsPerBlock][kI24], s_b[kMaxWarpsPerBlock][kI24], s_p[kMaxWarpsPerBlock][kI24 + 1];
-            int wid = threadIdx.x >> 5;
             Stage24 stg{s_w[wid], s_x[wid], s_y[wid], s_b[wid], s_p[wid]};
             U::run_warp(g, E, R, k, stg);
-        } else {
-            U::run(g, E, R, lane, 32, k);
+        }
+    } else {
+        // one warp per r-clique, its lanes striding the candidates
+        for (int64_t i = gwarp(); i < E.nA; i += nwarps()) {
+            int32_t R = E.A[i];
+            if (lane == 0) unmark_a(P, R);
+            Prep q;
+            int64_t n0 = U::prep(g, P, R, q);
+            if (n0 > kHeavy) {
+                int queued = 0;
+                if (lane == 0) {
+                    unsigned slot = atomicAdd(&P.ctl->nH, 1u);
+                    if (slot < P.hcap) {
+                        P.H[slot] = R;
+                        queued = 1;
+                    }
+                }
+                if (__shfl_sync(full, queued, 0)) continue;
+            }
+            for (int64_t j = lane; j < n0; j += 32) U::cand(g, E, R, q, j, k);
         }
     }
     add_counters(P.ctl, k);
@@ -875,7 +1004,7 @@ __device__ void phase_update_heavy(const GraphView& g, const PeelView<CT>& P) {
             for (unsigned h = blockIdx.x; h < nH; h += ns) U::run_block(g, E, P.H[h], k, stg);
         }
     } else {
-        for (unsigned h = blockIdx.x; h < nH; h += gridDim.x) U::run(g, E, P.H[h], threadIdx.x, blockDim.x, k);
+        for (unsigned h = blockIdx.x; h < nH; h += gridDim.x) run_all<U>(g, E, P.H[h], threadIdx.x, blockDim.x, k);
     }
     add_counters(P.ctl, k);
 }
@@ -961,11 +1090,42 @@ struct NoSerial {
     __device__ void operator()() const {}
 };
 
+// whether the round about to run its Update sorts A first (decided only in serial steps, so every
+// block reads the same value after the barrier)
+template <typename CT>
+__device__ __forceinline__ void decide_sort(PeelCtl* c, const PeelView<CT>* P) {
+    unsigned nA = (c->mode & ND_MODE_ADV) ? c->cntA : c->nA;
+    c->sorta = P->abits && !c->done && nA >= P->sort_min && nA <= P->cap;
+}
+
 template <typename CT>
 struct CtlSerial {
     PeelCtl* c;
     const PeelView<CT>* P;
-    __device__ void operator()() const { ctl_step(c, P->round_size, P->round_level, P->round_cap); }
+    __device__ void operator()() const {
+        ctl_step(c, P->round_size, P->round_level, P->round_cap);
+        decide_sort(c, P);  // same-level rounds; advance rounds decide after selecting A
+    }
+};
+
+template <typename CT>
+struct SortDecide {
+    PeelCtl* c;
+    const PeelView<CT>* P;
+    __device__ void operator()() const { decide_sort(c, P); }
+};
+
+// per-block member counts (hist[0 .. gridDim)) -> exclusive offsets
+struct SortScan {
+    PeelCtl* c;
+    __device__ void operator()() const {
+        unsigned long long run = 0;
+        for (unsigned b = 0; b < gridDim.x; ++b) {
+            unsigned long long v = c->hist[b];
+            c->hist[b] = run;
+            run += v;
+        }
+    }
 };
 
 // after the light Update: finish the round now unless heavy r-cliques are waiting
@@ -974,7 +1134,13 @@ struct CtlUnlessHeavy {
     PeelCtl* c;
     const PeelView<CT>* P;
     __device__ void operator()() const {
-        if (c->nH == 0) ctl_step(c, P->round_size, P->round_level, P->round_cap);
+        // the blocks branch on `heavy`, which only serial steps write: nH itself may already be
+        // growing in the next round's update by the time a slow block looks
+        c->heavy = c->nH != 0;
+        if (!c->heavy) {
+            ctl_step(c, P->round_size, P->round_level, P->round_cap);
+            decide_sort(c, P);
+        }
     }
 };
 
@@ -1005,11 +1171,17 @@ __global__ void __launch_bounds__(512, 2) k_peel_loop(GraphView g, PeelView<CT> 
                 if (!grid_barrier(c, target, NoSerial{})) return;
             }
             phase_adv_select(P);
+            if (!grid_barrier(c, target, SortDecide<CT>{c, &P})) return;
+        }
+        if (c->sorta) {
+            phase_sort_count(P);
+            if (!grid_barrier(c, target, SortScan{c})) return;
+            phase_sort_write(P);
             if (!grid_barrier(c, target, NoSerial{})) return;
         }
         phase_update<CT, U>(g, P);
         if (!grid_barrier(c, target, CtlUnlessHeavy<CT>{c, &P})) return;
-        if (c->nH) {
+        if (c->heavy) {
             phase_update_heavy<CT, U>(g, P);
             if (!grid_barrier(c, target, CtlSerial<CT>{c, &P})) return;
         }
