@@ -338,7 +338,7 @@ def main():
             "per_rs": {f"({r},{s})": {k: stats[(r, s)][k] for k in
                                       ("n_r", "n_s", "rho", "max_core", "listed", "decrements", "advances", "refills",
                                        "count_width", "t_orient_ms", "t_index_ms", "t_count_ms", "t_peel_ms",
-                                       "t_total_ms")} for r, s in wl["rs"]},
+                                       "t_total_ms", "t_phase_ms")} for r, s in wl["rs"]},
             "gpu_launches": launches,
             "roofline": roof,
             "clocks": clocks}

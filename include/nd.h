@@ -97,6 +97,10 @@ typedef struct nd_stats {
     double t_peel_ms;   /* the peeling loop */
     double t_total_ms;
     int64_t decrements; /* count decrements applied by Update over the run */
+    double t_phase_ms[6];/* persistent peel kernel only (zeros otherwise): wall time per phase as seen
+                            by block 0, barrier waits included: [0] level advance (minimum over the
+                            bucket window), [1] window refill, [2] selection of A, [3] id-order
+                            rebuild of A, [4] Update, [5] Update of the heavy r-cliques */
 } nd_stats;
 
 /* ---- context ------------------------------------------------------------------------- */

@@ -54,10 +54,13 @@ class nd_stats(ctypes.Structure):
                 ("max_core", ctypes.c_int64), ("listed", ctypes.c_int64), ("advances", ctypes.c_int64),
                 ("refills", ctypes.c_int64), ("count_width", ctypes.c_int32), ("orient_mode", ctypes.c_int32),
                 ("t_orient_ms", ctypes.c_double), ("t_index_ms", ctypes.c_double), ("t_count_ms", ctypes.c_double),
-                ("t_peel_ms", ctypes.c_double), ("t_total_ms", ctypes.c_double), ("decrements", ctypes.c_int64)]
+                ("t_peel_ms", ctypes.c_double), ("t_total_ms", ctypes.c_double), ("decrements", ctypes.c_int64),
+                ("t_phase_ms", ctypes.c_double * 6)]
 
     def as_dict(self) -> dict:
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["t_phase_ms"] = list(self.t_phase_ms)
+        return d
 
 
 class nd_request(ctypes.Structure):

@@ -807,6 +807,7 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
                                  4 * (int64_t)h.refills);
             po.listed = (int64_t)h.listed;
             po.decs = (int64_t)h.decs;
+            for (int i = 0; i < 6; ++i) po.phase_ms[i] = persistent_launches ? 1e-6 * (double)h.ph_ns[i] : 0.0;
             po.advances = h.advances;
             po.refills = h.refills;
             if (h.k > INT32_MAX && !rc) rc = nd_set_error(ND_EOVERFLOW, "a core number exceeds 2^31-1");
@@ -869,6 +870,7 @@ int nd_decompose_dev(nd_graph* g, int r, int s, int count_width, int flags, Peel
     S.max_core = po.max_core;
     S.listed = po.listed;
     S.decrements = po.decs;
+    for (int i = 0; i < 6; ++i) S.t_phase_ms[i] = po.phase_ms[i];
     S.advances = po.advances;
     S.refills = po.refills;
     S.count_width = w;

@@ -129,14 +129,16 @@ __device__ __forceinline__ uint32_t nd_hash_slot(int32_t w, int k) {
     return ((uint32_t)w * 0x9E3779B1u) >> (32 - k);  // multiplicative hashing (Knuth), top k bits
 }
 
-// triangle id stored for w in the table of 2^k slots, or -1
+// triangle id stored for w in the table of 2^k slots, or -1 (the first probe is a plain load, so
+// the compiler can issue the first probes of several lookups together)
 __device__ __forceinline__ int32_t nd_hash_find(const unsigned long long* __restrict__ tab, int k, int32_t w) {
     uint32_t mask = (1u << k) - 1u, s = nd_hash_slot(w, k);
+    unsigned long long v = __ldg(tab + s);
     for (uint32_t probes = 0; probes <= mask; ++probes) {
-        unsigned long long v = __ldg(tab + s);
         if (v == ND_HASH_EMPTY) return -1;
         if ((int32_t)(v >> 32) == w) return (int32_t)(v & 0xffffffffu);
         s = (s + 1) & mask;
+        v = __ldg(tab + s);
     }
     return -1;
 }
@@ -223,6 +225,9 @@ struct PeelCtl {
     unsigned long long listed;
     unsigned long long decs;
     long long advances, refills;
+    // persistent kernel: nanoseconds per phase between barriers, as seen by block 0
+    unsigned long long ph_ns[6];
+    unsigned long long ph_last;
     unsigned long long hist[ND_HBINS];
 };
 

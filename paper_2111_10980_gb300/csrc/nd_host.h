@@ -57,6 +57,7 @@ struct nd_graph {
 struct PeelOut {
     DBuf core, rnd;
     int64_t rho = 0, max_core = 0, listed = 0, decs = 0, advances = 0, refills = 0;
+    double phase_ms[6] = {0, 0, 0, 0, 0, 0};
     std::vector<int64_t> sizes, levels;
 };
 

@@ -115,6 +115,8 @@ __global__ void k_init(PeelCtl* c, int64_t n_r, int64_t max_rounds) {
         c->lmat = 0;
         c->heavy = 0;
         c->sorta = 0;
+        for (int i = 0; i < 6; ++i) c->ph_ns[i] = 0;
+        c->ph_last = 0;
         c->k = 0;
         c->hi = 0;
         c->finished = 0;
@@ -566,24 +568,21 @@ __device__ __forceinline__ void add_counters(PeelCtl* c, UpdCounters k) {
     }
 }
 
-// Each Update variant is a functor with
-//   work(g, R):                 length of the list that drives R's listing;
-//   run(g, E, R, j0, dj, lst):  lists the s-cliques containing R from driver entries
-//                               j0, j0 + dj, ... (lanes of one warp: j0 = lane, dj = 32;
-//                               the whole grid on one heavy R: j0 = global lane, dj = all lanes).
-// Work of one r-clique R: the driving list (b[0], n[0]) whose entries are the candidates, and the
-// lists they are searched in. prep() fills it and returns n[0]; cand() handles candidate j; run()
-// is threads j0, j0 + dj, ... over all candidates of one R.
+// Each Update variant is a functor. (1,2), (1,3), (2,3), (3,4) have
+//   prep(g, P, R, q): fills q with R's driving list (b[0], n[0]) -- its entries are the
+//                     candidates -- and the lists they are searched in; returns n[0];
+//   cand(g, E, R, q, j, k): lists the s-cliques of candidate j and applies Update-Func.
+// (2,4) stages N(u) ∩ N(v) instead (run_warp / run_block, below).
 struct Prep {
     int64_t b[3];
     int64_t n[3];
     int64_t h[3];  // (3,4): hash-table offset of the list, -1 when it is searched by bisection
 };
 
-// The light Update phase gives each warp one R at a time (its lanes share the R's lists, so the
-// upper levels of their searches hit the same lines) and defers R with work > kHeavy to a list
-// that the heavy phase gives one block each, so a few hub r-cliques in a round do not serialise
-// on single warps.
+// The light Update phase gives each warp one R at a time: its lanes share the R's lists and read
+// the driving list coalesced. R with more candidates than the variant's threshold go to a list
+// that the heavy phase gives one block each, so a few hub r-cliques do not serialise on single
+// warps.
 constexpr int64_t kHeavy = 4096;
 
 template <typename U, typename CT>
@@ -594,6 +593,7 @@ __device__ __forceinline__ void run_all(const GraphView& g, const RoundEnv<CT>& 
     for (int64_t j = j0; j < n0; j += dj) U::cand(g, E, R, q, j, k);
 }
 
+
 // (1,2): R = v; S = {v, w} for every neighbour w.
 template <typename CT>
 struct Upd12 {
@@ -602,7 +602,8 @@ struct Upd12 {
         q.n[0] = g.rp[v + 1] - q.b[0];
         return q.n[0];
     }
-    __device__ static void cand(const GraphView& g, const RoundEnv<CT>& E, int32_t v, const Prep& q, int64_t j,
+    template <typename Q>
+    __device__ static void cand(const GraphView& g, const RoundEnv<CT>& E, int32_t v, const Q& q, int64_t j,
                                 UpdCounters& k) {
         int32_t o[1] = {g.col[q.b[0] + j]};
         update_func<CT, 1>(E, v, o, k);
@@ -617,7 +618,8 @@ struct Upd13 {
         q.n[0] = g.rp[v + 1] - q.b[0];
         return q.n[0];
     }
-    __device__ static void cand(const GraphView& g, const RoundEnv<CT>& E, int32_t v, const Prep& q, int64_t j,
+    template <typename Q>
+    __device__ static void cand(const GraphView& g, const RoundEnv<CT>& E, int32_t v, const Q& q, int64_t j,
                                 UpdCounters& k) {
         int32_t w = g.col[q.b[0] + j];
         for (int64_t jx = g.dg_rp[w]; jx < g.dg_rp[w + 1]; ++jx) {
@@ -632,6 +634,7 @@ struct Upd13 {
 // (2,3): R = (u,v); S = {u, v, w} for w in N(u) ∩ N(v); the shorter row drives.
 template <typename CT>
 struct Upd23 {
+    static constexpr int64_t kHeavyWork = 256;  // a block, not a warp, for rows longer than this
     __device__ static int64_t work(const GraphView& g, int32_t R) {
         int32_t u = g.eu[R], v = g.ev[R];
         int64_t du = g.rp[u + 1] - g.rp[u], dv = g.rp[v + 1] - g.rp[v];
@@ -647,7 +650,8 @@ struct Upd23 {
         q.n[1] = u_drives ? vn : un;
         return q.n[0];
     }
-    __device__ static void cand(const GraphView& g, const RoundEnv<CT>& E, int32_t R, const Prep& q, int64_t j,
+    template <typename Q>
+    __device__ static void cand(const GraphView& g, const RoundEnv<CT>& E, int32_t R, const Q& q, int64_t j,
                                 UpdCounters& k) {
         // the edge to the candidate, peeled in an earlier round: every S through it is dead
         int64_t p = q.b[0] + j;
@@ -873,7 +877,8 @@ struct Upd34 {
         return q.n[0];
     }
     // the triangle R + w of list x (w's entry in L(e_x)) and its round; false when w is not there
-    __device__ static bool look(const GraphView& g, const RoundEnv<CT>& E, const Prep& q, int x, int32_t w,
+    template <typename Q>
+    __device__ static bool look(const GraphView& g, const RoundEnv<CT>& E, const Q& q, int x, int32_t w,
                                 int32_t& id, int32_t& r) {
         if (q.h[x] >= 0) {
             id = nd_hash_find(E.P.htab + q.h[x], nd_hash_bits(q.n[x]), w);
@@ -890,7 +895,8 @@ struct Upd34 {
     // S = R + w, w = entry j of list 0. Only the owner (smallest id of S's members in A) applies
     // S, so R stops as soon as a member in A with a smaller id is known: first the entry's own
     // triangle (read along the list), then the ones found in lists 1 and 2.
-    __device__ static void cand(const GraphView& g, const RoundEnv<CT>& E, int32_t R, const Prep& q, int64_t j,
+    template <typename Q>
+    __device__ static void cand(const GraphView& g, const RoundEnv<CT>& E, int32_t R, const Q& q, int64_t j,
                                 UpdCounters& k) {
         int32_t r0 = E.P.et_rnd[q.b[0] + j];
         if (r0 < E.t) return;
@@ -919,6 +925,7 @@ template <typename U>
 struct is_staged<U, decltype((void)U::kStaged)> {
     static constexpr bool value = U::kStaged;
 };
+
 
 template <typename U, typename = void>
 struct heavy_work {
@@ -962,13 +969,13 @@ __device__ void phase_update(const GraphView& g, const PeelView<CT>& P) {
             U::run_warp(g, E, R, k, stg);
         }
     } else {
-        // one warp per r-clique, its lanes striding the candidates
+        // one warp per r-clique: its lanes read the driving list coalesced
         for (int64_t i = gwarp(); i < E.nA; i += nwarps()) {
             int32_t R = E.A[i];
             if (lane == 0) unmark_a(P, R);
             Prep q;
             int64_t n0 = U::prep(g, P, R, q);
-            if (n0 > kHeavy) {
+            if (n0 > heavy_work<U>::value) {
                 int queued = 0;
                 if (lane == 0) {
                     unsigned slot = atomicAdd(&P.ctl->nH, 1u);
@@ -1156,12 +1163,23 @@ template <typename CT, typename U, bool k34>
 __global__ void __launch_bounds__(512, 2) k_peel_loop(GraphView g, PeelView<CT> P) {
     PeelCtl* c = P.ctl;
     unsigned long long target = 0;
+    bool timer = blockIdx.x == 0 && threadIdx.x == 0;
+    // block 0 books the time since the previous barrier to the phase that just ended
+    auto book = [&](int ph) {
+        if (timer) {
+            unsigned long long now = globaltimer();
+            c->ph_ns[ph] += now - c->ph_last;
+            c->ph_last = now;
+        }
+    };
     if (!grid_barrier(c, target, CtlSerial<CT>{c, &P})) return;  // set up round 0
+    if (timer) c->ph_last = globaltimer();
     for (;;) {
         if (c->done) return;  // every block reads the same value after the barrier
         if (c->mode & ND_MODE_ADV) {
             phase_adv_min(P);
             if (!grid_barrier(c, target, NoSerial{})) return;
+            book(0);
             if (need_refill(c)) {
                 phase_refill_scan(P);
                 if (!grid_barrier(c, target, NoSerial{})) return;
@@ -1169,21 +1187,26 @@ __global__ void __launch_bounds__(512, 2) k_peel_loop(GraphView g, PeelView<CT> 
                 if (!grid_barrier(c, target, PickSerial{c})) return;
                 phase_refill_select(P);
                 if (!grid_barrier(c, target, NoSerial{})) return;
+                book(1);
             }
             phase_adv_select(P);
             if (!grid_barrier(c, target, SortDecide<CT>{c, &P})) return;
+            book(2);
         }
         if (c->sorta) {
             phase_sort_count(P);
             if (!grid_barrier(c, target, SortScan{c})) return;
             phase_sort_write(P);
             if (!grid_barrier(c, target, NoSerial{})) return;
+            book(3);
         }
         phase_update<CT, U>(g, P);
         if (!grid_barrier(c, target, CtlUnlessHeavy<CT>{c, &P})) return;
+        book(4);
         if (c->heavy) {
             phase_update_heavy<CT, U>(g, P);
             if (!grid_barrier(c, target, CtlSerial<CT>{c, &P})) return;
+            book(5);
         }
     }
 }
