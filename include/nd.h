@@ -180,6 +180,12 @@ ND_API int nd_decompose(nd_graph *g, int r, int s, int count_width, int32_t *cor
  * Errors: ND_EINVAL (no decomposition yet). */
 ND_API int nd_rounds(nd_graph *g, int64_t *sizes_out, int64_t *levels_out, int64_t cap, int64_t *rho_out);
 
+/* Profiling aid (no counterpart in the paper): wall time in nanoseconds that the Update of each
+ * round of the last nd_decompose on this graph took, as block 0 of the persistent peel kernel saw
+ * it (barrier wait included): ns_out[t] for t < min(rho, cap). Zeros when the peel ran in another
+ * launch mode. Host pointer. Errors: ND_EINVAL (no decomposition yet). */
+ND_API int nd_round_times(nd_graph *g, int64_t *ns_out, int64_t cap);
+
 /* The r-cliques themselves (the inverse index map, Section 5.3): tuples_out receives n_r
  * ascending tuples of r int32 vertex ids in canonical order (host, or device with
  * ND_PTR_DEVICE; NULL to query n_r only). r in {1, 2, 3}. Errors: ND_EINVAL, ND_ENOMEM. */

@@ -38,7 +38,7 @@ STATUS_NAMES = {0: "ND_OK", 1: "ND_EINVAL", 2: "ND_ENOMEM", 3: "ND_EOVERFLOW", 4
 # every entry point declared in include/nd.h
 API = ["nd_ctx_create", "nd_ctx_set_allocator", "nd_ctx_destroy", "nd_ctx_bytes_in_use", "nd_kernel_launches", "nd_last_error",
        "nd_load_csr", "nd_graph_free", "nd_graph_size", "nd_orient", "nd_graph_reset", "nd_count", "nd_decompose",
-       "nd_rounds", "nd_rcliques", "nd_batch_run", "nd_server_create", "nd_submit", "nd_poll", "nd_server_drain",
+       "nd_rounds", "nd_round_times", "nd_rcliques", "nd_batch_run", "nd_server_create", "nd_submit", "nd_poll", "nd_server_drain",
        "nd_server_destroy", "nd_kcore_noalloc"]
 ND_NOALLOC_MAX_VERTICES = 262144
 
@@ -129,6 +129,7 @@ def lib() -> ctypes.CDLL:
         L.nd_decompose.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_int,
                                    ctypes.POINTER(nd_stats)]
         L.nd_rounds.argtypes = [vp, vp, vp, i64, i64p]
+        L.nd_round_times.argtypes = [vp, vp, i64]
         L.nd_rcliques.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, i64p]
         L.nd_kcore_noalloc.argtypes = [i32, vp, vp, vp, vp]
         L.nd_batch_run.argtypes = [vp, ctypes.POINTER(nd_request), i32, ctypes.POINTER(nd_batch_stats)]
@@ -326,6 +327,16 @@ def nd_rounds(g: Handle, cap: int | None = None):
     _check(lib().nd_rounds(g.ptr, ctypes.c_void_p(sizes.ctypes.data), ctypes.c_void_p(levels.ctypes.data), k,
                            ctypes.byref(rho)))
     return sizes[:k], levels[:k], rho.value
+
+
+def nd_round_times(g: Handle, cap: int | None = None) -> np.ndarray:
+    """Update wall time per round (ns) of the last decomposition on g (nd.h: nd_round_times)."""
+    rho = ctypes.c_int64()
+    _check(lib().nd_rounds(g.ptr, None, None, 0, ctypes.byref(rho)))
+    k = rho.value if cap is None else min(cap, rho.value)
+    out = np.zeros(max(k, 1), np.int64)
+    _check(lib().nd_round_times(g.ptr, ctypes.c_void_p(out.ctypes.data), k))
+    return out[:k]
 
 
 def nd_rcliques(g: Handle, r: int, out=None):

@@ -597,7 +597,7 @@ extern "C" int nd_count(nd_graph* g, int r, int s, int count_width, void* counts
 
 // Hash directory of the triangle lists for the (3,4) Update: table offsets per edge (an exclusive
 // scan of the per-list slot counts) and the tables, filled from the index.
-static int build_tri_hash(nd_graph* g, DBuf& hoff, DBuf& htab) {
+static int build_tri_hash(nd_graph* g, DBuf& hoff, DBuf& htab, DBuf& hpos) {
     nd_ctx* c = g->ctx;
     cudaStream_t st = c->stream;
     int64_t m = g->m;
@@ -617,10 +617,12 @@ static int build_tri_hash(nd_graph* g, DBuf& hoff, DBuf& htab) {
     if (!rc) rc = read_back(g, (int64_t*)hoff.p + m, &total, "triangle hash");
     nd_free(c, slots);
     nd_free(c, tmp);
-    if (!rc) rc = nd_alloc(c, htab, sizeof(unsigned long long) * std::max<int64_t>(total, 1));
+    if (!rc) rc = nd_alloc(c, htab, sizeof(NdHashSlot) * std::max<int64_t>(total, 1));
+    if (!rc) rc = nd_alloc(c, hpos, sizeof(int32_t) * std::max<int64_t>(3 * g->n3, 1));
     if (rc) return rc;
     ND_CUDA(cudaMemsetAsync(htab.p, 0xff, htab.bytes, st));
-    nd_tri_hash_fill(v, (const int64_t*)hoff.p, (unsigned long long*)htab.p, st);
+    ND_CUDA(cudaMemsetAsync(hpos.p, 0xff, hpos.bytes, st));
+    nd_tri_hash_fill(v, (const int64_t*)hoff.p, (NdHashSlot*)htab.p, (int32_t*)hpos.p, st);
     return nd_check_launch("triangle hash");
 }
 
@@ -648,14 +650,14 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
         hstage = g->edge_mindeg;
         hslices = nd_peel_heavy_slices();
     }
-    DBuf ctl, A0, A1, N0, N1, L0, L1, H, rs, rl, etr, hsc, abits, hoff, htab;
+    DBuf ctl, A0, A1, N0, N1, L0, L1, H, rs, rl, rt, etr, hsc, abits, hoff, htab, hpos;
     if ((rc = nd_alloc(c, ctl, sizeof(PeelCtl))) || (rc = nd_alloc(c, A0, 4 * cap)) || (rc = nd_alloc(c, A1, 4 * cap)) ||
         (rc = nd_alloc(c, N0, 4 * cap)) || (rc = nd_alloc(c, N1, 4 * cap)) || (rc = nd_alloc(c, L0, 4 * cap)) ||
         (rc = nd_alloc(c, L1, 4 * cap)) || (rc = nd_alloc(c, H, 4 * hcap)) || (rc = nd_alloc(c, rs, 8 * rcap)) ||
-        (rc = nd_alloc(c, rl, 8 * rcap)) || (r == 3 && (rc = nd_alloc(c, etr, 4 * std::max<int64_t>(3 * g->n3, 1)))) ||
+        (rc = nd_alloc(c, rl, 8 * rcap)) || (rc = nd_alloc(c, rt, 8 * rcap)) || (r == 3 && (rc = nd_alloc(c, etr, 4 * std::max<int64_t>(3 * g->n3, 1)))) ||
         (staged && (rc = nd_alloc(c, hsc, 4 * 5 * (hstage + 1) * hslices))) ||
-        (rc = nd_alloc(c, abits, 4 * ((cap + 31) / 32)))) {
-        for (DBuf* b : {&ctl, &A0, &A1, &N0, &N1, &L0, &L1, &H, &rs, &rl, &etr, &hsc, &abits, &hoff, &htab}) nd_free(c, *b);
+        (rc = nd_alloc(c, abits, r == 3 ? 4 * ((cap + 31) / 32) : 4))) {
+        for (DBuf* b : {&ctl, &A0, &A1, &N0, &N1, &L0, &L1, &H, &rs, &rl, &rt, &etr, &hsc, &abits, &hoff, &htab, &hpos}) nd_free(c, *b);
         return rc;
     }
     PeelView<CT> P;
@@ -673,7 +675,9 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
     P.hscratch = (int32_t*)hsc.p;
     P.hstage = hstage;
     P.hslices = (int32_t)hslices;
-    P.abits = (uint32_t*)abits.p;
+    // id-order rebuilds of A pay off for triangles (their lists are long); edges and vertices
+    // skip them
+    P.abits = r == 3 ? (uint32_t*)abits.p : nullptr;
     // a round sorts A when it holds at least 1/8192 of the r-cliques (and 2048): then the two
     // passes over the bitmap cost little next to the Update they make cache-friendly
     P.sort_min = (uint32_t)std::max<int64_t>(n_r / 8192, 2048);
@@ -682,6 +686,8 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
     P.ctl = (PeelCtl*)ctl.p;
     P.round_size = (int64_t*)rs.p;
     P.round_level = (int64_t*)rl.p;
+    P.round_ns = (int64_t*)rt.p;
+    cudaMemsetAsync(rt.p, 0, rt.bytes, st);
     P.round_cap = rcap;
     P.et_rnd = nullptr;
     P.tri_e = nullptr;
@@ -689,14 +695,16 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
     P.et_rp = nullptr;
     P.hoff = nullptr;
     P.htab = nullptr;
-    if (r == 3 && (rc = build_tri_hash(g, hoff, htab))) {
-        for (DBuf* b : {&ctl, &A0, &A1, &N0, &N1, &L0, &L1, &H, &rs, &rl, &etr, &hsc, &abits, &hoff, &htab})
+    P.hpos = nullptr;
+    if (r == 3 && (rc = build_tri_hash(g, hoff, htab, hpos))) {
+        for (DBuf* b : {&ctl, &A0, &A1, &N0, &N1, &L0, &L1, &H, &rs, &rl, &rt, &etr, &hsc, &abits, &hoff, &htab, &hpos})
             nd_free(c, *b);
         return rc;
     }
     if (r == 3) {
         P.hoff = (const int64_t*)hoff.p;
-        P.htab = (const unsigned long long*)htab.p;
+        P.htab = (NdHashSlot*)htab.p;
+        P.hpos = (const int32_t*)hpos.p;
         P.et_rnd = (int32_t*)etr.p;
         P.tri_e = (const int32_t*)g->tri_e.p;
         P.tri_pos = (const int32_t*)g->tri_pos.p;
@@ -817,13 +825,15 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
         int64_t nrec = std::min<int64_t>(po.rho, rcap);
         po.sizes.resize(nrec);
         po.levels.resize(nrec);
+        po.round_ns.resize(nrec);
         if (nrec) {
             cudaMemcpyAsync(po.sizes.data(), rs.p, 8 * nrec, cudaMemcpyDeviceToHost, st);
             cudaMemcpyAsync(po.levels.data(), rl.p, 8 * nrec, cudaMemcpyDeviceToHost, st);
+            cudaMemcpyAsync(po.round_ns.data(), rt.p, 8 * nrec, cudaMemcpyDeviceToHost, st);
             rc = nd_sync(c, "peel record");
         }
     }
-    for (DBuf* b : {&ctl, &A0, &A1, &N0, &N1, &L0, &L1, &H, &rs, &rl, &etr, &hsc, &abits, &hoff, &htab}) nd_free(c, *b);
+    for (DBuf* b : {&ctl, &A0, &A1, &N0, &N1, &L0, &L1, &H, &rs, &rl, &rt, &etr, &hsc, &abits, &hoff, &htab, &hpos}) nd_free(c, *b);
     return rc;
 }
 
@@ -903,6 +913,7 @@ extern "C" int nd_decompose(nd_graph* g, int r, int s, int count_width, int32_t*
         if (!rc) rc = nd_sync(c, "nd_decompose");
         g->last_sizes = po.sizes;
         g->last_levels = po.levels;
+        g->last_round_ns = po.round_ns;
         g->last_rho = po.rho;
         g->have_last = true;
     }
@@ -920,6 +931,15 @@ extern "C" int nd_rounds(nd_graph* g, int64_t* sizes_out, int64_t* levels_out, i
         if (levels_out) levels_out[i] = g->last_levels[i];
     }
     if (rho_out) *rho_out = g->last_rho;
+    return ND_OK;
+}
+
+extern "C" int nd_round_times(nd_graph* g, int64_t* ns_out, int64_t cap) {
+    if (!g) return nd_set_error(ND_EINVAL, "nd_round_times: NULL graph");
+    if (!g->have_last) return nd_set_error(ND_EINVAL, "nd_round_times: no decomposition has run on this graph");
+    int64_t k = std::min<int64_t>(cap, (int64_t)g->last_round_ns.size());
+    for (int64_t i = 0; i < k; ++i)
+        if (ns_out) ns_out[i] = g->last_round_ns[i];
     return ND_OK;
 }
 

@@ -113,9 +113,16 @@ __device__ __forceinline__ void nd_warp_merge(const int32_t* __restrict__ A, int
 
 // Hash directory of the triangle lists (built for a (3,4) peel): list L(e) with more than
 // ND_HASH_MIN entries gets an open-addressing table of 2^k >= 2 |L(e)| slots (load <= 1/2),
-// linear probing; a slot holds (vertex w << 32) | triangle id, ND_HASH_EMPTY when free.
+// linear probing. A slot holds the entry's vertex w, its triangle's id and the triangle's peel
+// round (kept current by the peel, like the list tags), so one 16-byte load answers a lookup.
 #define ND_HASH_MIN 32
-#define ND_HASH_EMPTY 0xffffffffffffffffull
+
+struct __align__(16) NdHashSlot {
+    int32_t w;    // -1: free
+    int32_t id;
+    int32_t rnd;
+    int32_t pad;
+};
 
 __host__ __device__ __forceinline__ bool nd_hashed(int64_t n) { return n > ND_HASH_MIN && n <= ((int64_t)1 << 30); }
 
@@ -129,18 +136,38 @@ __device__ __forceinline__ uint32_t nd_hash_slot(int32_t w, int k) {
     return ((uint32_t)w * 0x9E3779B1u) >> (32 - k);  // multiplicative hashing (Knuth), top k bits
 }
 
-// triangle id stored for w in the table of 2^k slots, or -1 (the first probe is a plain load, so
-// the compiler can issue the first probes of several lookups together)
-__device__ __forceinline__ int32_t nd_hash_find(const unsigned long long* __restrict__ tab, int k, int32_t w) {
-    uint32_t mask = (1u << k) - 1u, s = nd_hash_slot(w, k);
-    unsigned long long v = __ldg(tab + s);
+// Continue a lookup whose first probe (slot s, contents v) was loaded by the caller.
+__device__ __forceinline__ bool nd_hash_resolve(const NdHashSlot* tab, int k, int32_t w, uint32_t s, int4 v,
+                                                int32_t& id, int32_t& rnd) {
+    uint32_t mask = (1u << k) - 1u;
     for (uint32_t probes = 0; probes <= mask; ++probes) {
-        if (v == ND_HASH_EMPTY) return -1;
-        if ((int32_t)(v >> 32) == w) return (int32_t)(v & 0xffffffffu);
+        if (v.x == w) {
+            id = v.y;
+            rnd = v.z;
+            return true;
+        }
+        if (v.x == -1) return false;
         s = (s + 1) & mask;
-        v = __ldg(tab + s);
+        v = *reinterpret_cast<const int4*>(tab + s);
     }
-    return -1;
+    return false;
+}
+
+// The slot of w in the table of 2^k slots: id and round of its triangle; false if w is absent.
+// Plain (coherent) loads: the round field changes while the peel runs.
+__device__ __forceinline__ bool nd_hash_find(const NdHashSlot* tab, int k, int32_t w, int32_t& id, int32_t& rnd) {
+    uint32_t mask = (1u << k) - 1u, s = nd_hash_slot(w, k);
+    for (uint32_t probes = 0; probes <= mask; ++probes) {
+        int4 v = *reinterpret_cast<const int4*>(tab + s);
+        if (v.x == w) {
+            id = v.y;
+            rnd = v.z;
+            return true;
+        }
+        if (v.x == -1) return false;
+        s = (s + 1) & mask;
+    }
+    return false;
 }
 
 // Use the warp merge when the longer list is at most this many times the shorter one (plus a
@@ -248,9 +275,11 @@ struct PeelView {
     // membership bitmap of A (NULL: never sorted) and the |A| from which a round sorts A
     uint32_t* abits;
     uint32_t sort_min;
-    // (3,4): hash directory of the triangle lists (table offset per edge, tables), or NULL
+    // (3,4): hash directory of the triangle lists (table offset per edge, tables, and for each
+    // triangle and each of its three lists the slot holding it, -1 in a list without a table)
     const int64_t* hoff;
-    const unsigned long long* htab;
+    NdHashSlot* htab;
+    const int32_t* hpos;
     // (3,4) only: the round tag of every triangle-index entry, and what is needed to find the
     // three entries of a triangle (NULL for other (r,s))
     int32_t* et_rnd;
@@ -261,6 +290,7 @@ struct PeelView {
     PeelCtl* ctl;
     int64_t* round_size;
     int64_t* round_level;
+    int64_t* round_ns;      // persistent kernel: Update wall time per round (block 0), or NULL
     int64_t round_cap;
 };
 
@@ -309,7 +339,7 @@ void nd_edge_tuples(const GraphView& g, int32_t* out, cudaStream_t st);
 void nd_max_edge_mindeg(const GraphView& g, unsigned long long* out, cudaStream_t st);
 // hash directory of the triangle lists: slots per edge (0 for short lists), then the tables
 void nd_tri_hash_sizes(const GraphView& g, int64_t* slots, cudaStream_t st);
-void nd_tri_hash_fill(const GraphView& g, const int64_t* hoff, unsigned long long* tab, cudaStream_t st);
+void nd_tri_hash_fill(const GraphView& g, const int64_t* hoff, NdHashSlot* tab, int32_t* hpos, cudaStream_t st);
 // blocks of the (2,4) heavy phase that hold a scratch slice; the others skip the phase
 int nd_peel_heavy_slices();
 

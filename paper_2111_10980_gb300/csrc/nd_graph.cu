@@ -300,8 +300,10 @@ __global__ void k_tri_hash_sizes(GraphView g, int64_t* __restrict__ slots) {
     }
 }
 
-// one warp per long list; each entry claims a free slot by compare-and-swap
-__global__ void k_tri_hash_fill(GraphView g, const int64_t* __restrict__ hoff, unsigned long long* __restrict__ tab) {
+// one warp per long list; each entry claims a free slot by compare-and-swap on its (w, id) half,
+// then sets the round field to unpeeled and records the slot for its triangle (hpos)
+__global__ void k_tri_hash_fill(GraphView g, const int64_t* __restrict__ hoff, NdHashSlot* __restrict__ tab,
+                                int32_t* __restrict__ hpos) {
     int lane = threadIdx.x & 31;
     for (int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < g.m;
          e += ((int64_t)gridDim.x * blockDim.x) >> 5) {
@@ -309,13 +311,19 @@ __global__ void k_tri_hash_fill(GraphView g, const int64_t* __restrict__ hoff, u
         if (!nd_hashed(n)) continue;
         int k = nd_hash_bits(n);
         uint32_t mask = (1u << k) - 1u;
-        unsigned long long* t = tab + hoff[e];
+        NdHashSlot* t = tab + hoff[e];
         for (int64_t p = lane; p < n; p += 32) {
-            int32_t w = g.et_w[b + p];
-            unsigned long long v = ((unsigned long long)(uint32_t)w << 32) | (uint32_t)g.et_t[b + p];
+            int32_t w = g.et_w[b + p], id = g.et_t[b + p];
+            unsigned long long key = ((unsigned long long)(uint32_t)id << 32) | (uint32_t)w;  // little endian: w first
             uint32_t s = nd_hash_slot(w, k);
             for (uint32_t probes = 0; probes <= mask; ++probes) {
-                if (atomicCAS(t + s, ND_HASH_EMPTY, v) == ND_HASH_EMPTY) break;
+                unsigned long long* half = reinterpret_cast<unsigned long long*>(t + s);
+                if (atomicCAS(half, 0xffffffffffffffffull, key) == 0xffffffffffffffffull) {
+                    t[s].rnd = ND_UNPEELED;
+                    int x = g.tri_e[3 * (int64_t)id] == e ? 0 : (g.tri_e[3 * (int64_t)id + 1] == e ? 1 : 2);
+                    hpos[3 * (int64_t)id + x] = (int32_t)s;
+                    break;
+                }
                 s = (s + 1) & mask;
             }
         }
@@ -329,9 +337,9 @@ void nd_tri_hash_sizes(const GraphView& g, int64_t* slots, cudaStream_t st) {
     ND_K(k_tri_hash_sizes<<<blocks_for_threads(g.m), kThreads, 0, st>>>(g, slots));
 }
 
-void nd_tri_hash_fill(const GraphView& g, const int64_t* hoff, unsigned long long* tab, cudaStream_t st) {
+void nd_tri_hash_fill(const GraphView& g, const int64_t* hoff, NdHashSlot* tab, int32_t* hpos, cudaStream_t st) {
     if (g.m <= 0) return;
-    ND_K(k_tri_hash_fill<<<blocks_for_warps(g.m), kThreads, 0, st>>>(g, hoff, tab));
+    ND_K(k_tri_hash_fill<<<blocks_for_warps(g.m), kThreads, 0, st>>>(g, hoff, tab, hpos));
 }
 
 void nd_max_edge_mindeg(const GraphView& g, unsigned long long* out, cudaStream_t st) {

@@ -51,14 +51,14 @@ struct nd_graph {
     // record of the last decomposition
     bool have_last = false;
     int64_t last_rho = 0;
-    std::vector<int64_t> last_sizes, last_levels;
+    std::vector<int64_t> last_sizes, last_levels, last_round_ns;
 };
 
 struct PeelOut {
     DBuf core, rnd;
     int64_t rho = 0, max_core = 0, listed = 0, decs = 0, advances = 0, refills = 0;
     double phase_ms[6] = {0, 0, 0, 0, 0, 0};
-    std::vector<int64_t> sizes, levels;
+    std::vector<int64_t> sizes, levels, round_ns;
 };
 
 int nd_set_error(int code, const char* fmt, ...);

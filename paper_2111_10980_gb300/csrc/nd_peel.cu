@@ -55,14 +55,25 @@ __device__ __forceinline__ int64_t knew_of(const PeelCtl* c) {
 // parameter block to local memory)
 __device__ __forceinline__ int32_t* pick(int32_t* const (&a)[2], int i) { return i ? a[1] : a[0]; }
 
-// (3,4): tag the three index entries of triangle R with the round in which it is peeled.
+// (3,4): tag the three index entries of triangle R (and its hash-directory slots) with the round
+// in which it is peeled. Out of line with plain pointer arguments: it runs once per triangle, and
+// inlined into Update's decrement path it would cost registers there.
+__device__ __noinline__ void tri_round_write(const int32_t* tri_e, const int64_t* et_rp, const int32_t* tri_pos,
+                                             int32_t* et_rnd, const int32_t* hpos, const int64_t* hoff,
+                                             NdHashSlot* htab, int64_t R, int32_t round) {
+    for (int x = 0; x < 3; ++x) {
+        int32_t e = tri_e[3 * R + x];
+        et_rnd[et_rp[e] + tri_pos[3 * R + x]] = round;
+        if (hpos) {
+            int32_t s = hpos[3 * R + x];
+            if (s >= 0) htab[hoff[e] + s].rnd = round;
+        }
+    }
+}
+
 template <typename CT>
 __device__ __forceinline__ void set_tri_round(const PeelView<CT>& P, int64_t R, int32_t round) {
-#pragma unroll
-    for (int x = 0; x < 3; ++x) {
-        int32_t e = P.tri_e[3 * R + x];
-        P.et_rnd[P.et_rp[e] + P.tri_pos[3 * R + x]] = round;
-    }
+    tri_round_write(P.tri_e, P.et_rp, P.tri_pos, P.et_rnd, P.hpos, P.hoff, P.htab, R, round);
 }
 
 // Membership bitmap of the next / current A (bit x set while x is scheduled and not yet updated):
@@ -881,9 +892,7 @@ struct Upd34 {
     __device__ static bool look(const GraphView& g, const RoundEnv<CT>& E, const Q& q, int x, int32_t w,
                                 int32_t& id, int32_t& r) {
         if (q.h[x] >= 0) {
-            id = nd_hash_find(E.P.htab + q.h[x], nd_hash_bits(q.n[x]), w);
-            if (id < 0) return false;
-            r = E.P.rnd[id];
+            if (!nd_hash_find(E.P.htab + q.h[x], nd_hash_bits(q.n[x]), w, id, r)) return false;
         } else {
             int64_t i = nd_find(g.et_w + q.b[x], q.n[x], w);
             if (i < 0) return false;
@@ -915,6 +924,77 @@ struct Upd34 {
         if (r1 != E.t) after_dec(E, id1, o1);
         if (r2 != E.t) after_dec(E, id2, o2);
     }
+
+    // Both search lists hashed: candidates j and j + 32 of this lane at once, each step issuing
+    // the loads of both before using any (the loop is bound by memory latency, so two chains in
+    // flight per lane nearly halve its time): list-0 entries, first probes of lists 1 and 2,
+    // then the decrements.
+    static constexpr bool kPair = true;
+    template <typename Q>
+    __device__ static void cand2(const GraphView& g, const RoundEnv<CT>& E, int32_t R, const Q& q, int64_t j,
+                                 UpdCounters& k) {
+        const int64_t b0 = q.b[0];
+        const bool vb = j + 32 < q.n[0];
+        int32_t ra = E.P.et_rnd[b0 + j], ia = g.et_t[b0 + j], wa = g.et_w[b0 + j];
+        int32_t rb = -1, ib = 0, wb = 0;
+        if (vb) {
+            rb = E.P.et_rnd[b0 + j + 32];
+            ib = g.et_t[b0 + j + 32];
+            wb = g.et_w[b0 + j + 32];
+        }
+        bool la = ra >= E.t && !(ra == E.t && ia < R);
+        bool lb = vb && rb >= E.t && !(rb == E.t && ib < R);
+        if (!la && !lb) return;
+        const NdHashSlot* t1 = E.P.htab + q.h[1];
+        const NdHashSlot* t2 = E.P.htab + q.h[2];
+        const int k1 = nd_hash_bits(q.n[1]), k2 = nd_hash_bits(q.n[2]);
+        uint32_t sa1 = nd_hash_slot(wa, k1), sa2 = nd_hash_slot(wa, k2);
+        uint32_t sb1 = nd_hash_slot(wb, k1), sb2 = nd_hash_slot(wb, k2);
+        int4 pa1 = make_int4(-1, 0, 0, 0), pa2 = pa1, pb1 = pa1, pb2 = pa1;
+        if (la) {
+            pa1 = *reinterpret_cast<const int4*>(t1 + sa1);
+            pa2 = *reinterpret_cast<const int4*>(t2 + sa2);
+        }
+        if (lb) {
+            pb1 = *reinterpret_cast<const int4*>(t1 + sb1);
+            pb2 = *reinterpret_cast<const int4*>(t2 + sb2);
+        }
+        int32_t ia1 = 0, ra1 = 0, ia2 = 0, ra2 = 0, ib1 = 0, rb1 = 0, ib2 = 0, rb2 = 0;
+        la = la && nd_hash_resolve(t1, k1, wa, sa1, pa1, ia1, ra1) && nd_hash_resolve(t2, k2, wa, sa2, pa2, ia2, ra2);
+        lb = lb && nd_hash_resolve(t1, k1, wb, sb1, pb1, ib1, rb1) && nd_hash_resolve(t2, k2, wb, sb2, pb2, ib2, rb2);
+        la = la && ra1 >= E.t && !(ra1 == E.t && ia1 < R) && ra2 >= E.t && !(ra2 == E.t && ia2 < R);
+        lb = lb && rb1 >= E.t && !(rb1 == E.t && ib1 < R) && rb2 >= E.t && !(rb2 == E.t && ib2 < R);
+        // decrements of both 4-cliques go out before any result is looked at
+        int64_t oa0 = la && ra != E.t ? nd_atomic_dec(&E.P.cnt[ia]) : 0;
+        int64_t oa1 = la && ra1 != E.t ? nd_atomic_dec(&E.P.cnt[ia1]) : 0;
+        int64_t oa2 = la && ra2 != E.t ? nd_atomic_dec(&E.P.cnt[ia2]) : 0;
+        int64_t ob0 = lb && rb != E.t ? nd_atomic_dec(&E.P.cnt[ib]) : 0;
+        int64_t ob1 = lb && rb1 != E.t ? nd_atomic_dec(&E.P.cnt[ib1]) : 0;
+        int64_t ob2 = lb && rb2 != E.t ? nd_atomic_dec(&E.P.cnt[ib2]) : 0;
+        if (la) {
+            k.listed++;
+            k.decs += (ra != E.t) + (ra1 != E.t) + (ra2 != E.t);
+            if (ra != E.t) after_dec(E, ia, oa0);
+            if (ra1 != E.t) after_dec(E, ia1, oa1);
+            if (ra2 != E.t) after_dec(E, ia2, oa2);
+        }
+        if (lb) {
+            k.listed++;
+            k.decs += (rb != E.t) + (rb1 != E.t) + (rb2 != E.t);
+            if (rb != E.t) after_dec(E, ib, ob0);
+            if (rb1 != E.t) after_dec(E, ib1, ob1);
+            if (rb2 != E.t) after_dec(E, ib2, ob2);
+        }
+    }
+};
+
+template <typename U, typename = void>
+struct has_pair {
+    static constexpr bool value = false;
+};
+template <typename U>
+struct has_pair<U, decltype((void)U::kPair)> {
+    static constexpr bool value = U::kPair;
 };
 
 template <typename U, typename = void>
@@ -985,6 +1065,12 @@ __device__ void phase_update(const GraphView& g, const PeelView<CT>& P) {
                     }
                 }
                 if (__shfl_sync(full, queued, 0)) continue;
+            }
+            if constexpr (has_pair<U>::value) {
+                if (q.h[1] >= 0 && q.h[2] >= 0) {
+                    for (int64_t j = lane; j < n0; j += 64) U::cand2(g, E, R, q, j, k);
+                    continue;
+                }
             }
             for (int64_t j = lane; j < n0; j += 32) U::cand(g, E, R, q, j, k);
         }
@@ -1164,18 +1250,22 @@ __global__ void __launch_bounds__(512, 2) k_peel_loop(GraphView g, PeelView<CT> 
     PeelCtl* c = P.ctl;
     unsigned long long target = 0;
     bool timer = blockIdx.x == 0 && threadIdx.x == 0;
-    // block 0 books the time since the previous barrier to the phase that just ended
+    int32_t tr = 0;  // the round being run
+    // block 0 books the time since the previous barrier to the phase that just ended (and the
+    // Update phases also to the round)
     auto book = [&](int ph) {
         if (timer) {
-            unsigned long long now = globaltimer();
-            c->ph_ns[ph] += now - c->ph_last;
+            unsigned long long now = globaltimer(), d = now - c->ph_last;
+            c->ph_ns[ph] += d;
             c->ph_last = now;
+            if (ph >= 4 && P.round_ns && tr < P.round_cap) P.round_ns[tr] += (int64_t)d;
         }
     };
     if (!grid_barrier(c, target, CtlSerial<CT>{c, &P})) return;  // set up round 0
     if (timer) c->ph_last = globaltimer();
     for (;;) {
         if (c->done) return;  // every block reads the same value after the barrier
+        tr = c->t;
         if (c->mode & ND_MODE_ADV) {
             phase_adv_min(P);
             if (!grid_barrier(c, target, NoSerial{})) return;

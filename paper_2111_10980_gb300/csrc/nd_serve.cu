@@ -199,8 +199,9 @@ size_t estimate_bytes(const nd_request& q) {
         }
         nr = std::min(w / 3.0, m * std::sqrt(2.0 * m) / 3.0);
         // per-edge table bounds + three entries per triangle; the peel adds the lists' hash
-        // directory (at most 4 slots of 8 bytes per entry) and an offset per edge
-        bytes += 16 * m + 48 * nr + 8 * m + 96 * nr;
+        // directory (at most 4 slots of 16 bytes per entry, a slot index per entry) and an offset
+        // per edge
+        bytes += 16 * m + 48 * nr + 8 * m + 204 * nr;
     }
     bytes += 40 * nr + 64 * 1024;  // counts, rounds, cores, work lists, control block
     return (size_t)bytes;

@@ -130,7 +130,7 @@ def test_server_overlapping_workers_equal_alone(nd, ctx):
 def test_server_memory_budget_and_queue(nd, ctx):
     items = mixed_graphs(12, 13)
     # a tight budget admits only a few small requests at a time; results are unchanged
-    tickets, outs, results = _serve(nd, ctx, items, workers=2, max_batch=8, mem_budget=4 << 20)
+    tickets, outs, results = _serve(nd, ctx, items, workers=2, max_batch=8, mem_budget=8 << 20)
     for (g, r, s), t, (out, k) in zip(items, tickets, outs):
         assert results[t][0] == nd.ND_OK
         assert np.array_equal(out[:k], orc.decompose(g, r, s).core)
