@@ -262,6 +262,7 @@ def main():
         wl["gen"] = lambda: gg.rmat(sc, 16, 0.57, 0.19, 0.19, seed=2)
         wl["desc"] = wl["desc"].replace("scale 20", f"scale {sc}")
         workload_name = f"rmat{sc}"
+    wl["name"] = workload_name
     g = wl["gen"]()
     stream = torch.cuda.Stream(device=local)
     ctx = nd.nd_ctx_create(local, stream=stream)
@@ -363,6 +364,33 @@ def main():
     return 0
 
 
+# DRAM bytes per launch (read + write) from one-pass ncu captures of the bench workloads (metrics
+# dram__bytes_read.sum and dram__bytes_write.sum over every launch of one warm-up and one timed
+# step), keyed by the fingerprint of the library sources they were taken on; reported as
+# roofline.traffic only while the sources still match.
+NCU_TRAFFIC = {
+    "293aa86a6755305f": {
+        ("rmat20", "k_peel_loop(3,4)"): 7.860e12,
+        ("rmat20", "k_peel_loop(2,3)"): 115.5e9,
+        ("rmat20", "k_count34"): 1158.9e9,
+        ("rmat20", "k_count23"): 9.6e9,
+    },
+}
+
+
+def sources_fingerprint():
+    import glob
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2111_10980_gb300", "csrc", "*"))):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(os.path.basename(f).encode())
+            with open(f, "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def roofline(wl, per_step_stats, g):
     """HBM roofline of the dominant kernel (largest share of the step, from the library's CUDA
     events on the launching stream), with the algorithmic-byte models stated in the design doc.
@@ -398,17 +426,27 @@ def roofline(wl, per_step_stats, g):
             # peel: per edge endpoints + row bounds (40 B); per destroyed triangle the two other
             # edge ids and their rounds (16 B); per decrement read + write (8 B)
             peel_b = 40 * n_r + 16 * destroyed + 8 * decs
+        elif (r, s) == (2, 4):
+            w = st["count_width"]
+            # count (DG listing): per edge its DG entry (8 B) and count (w B); per 4-clique the
+            # fourth vertex's DG entry (8 B) and its six edge counts (read + write, 2w B each)
+            count_b = (8 + w) * n_r + (8 + 12 * w) * n_s
+            # peel: per edge endpoints + row bounds (40 B); per destroyed 4-clique the DG entry of
+            # its last edge (8 B) and the rounds of its five other edges (20 B); per decrement a
+            # count read + write
+            peel_b = 40 * n_r + 28 * destroyed + 2 * w * decs
         else:
             count_b = peel_b = 0
         entries.append(("k_count%d%d" % (r, s), count_b, t_count))
         entries.append(("k_peel_loop(%d,%d)" % (r, s), peel_b, t_peel))
     entries.sort(key=lambda e: -e[2])
+    traffic = NCU_TRAFFIC.get(sources_fingerprint(), {})
 
     def one(name, b, t):
         a = b / t / 1e9 if t > 0 else 0.0
         return {"bound": "hbm", "kernel": name, "achieved": a, "peak": peak, "unit": "GB/s", "frac": a / peak,
-                "traffic": None, "peak_source": src + " (hbm_gbs)", "algorithmic_bytes_per_launch": b,
-                "avg_launch_ms": 1000.0 * t}
+                "traffic": traffic.get((wl.get("name"), name)), "peak_source": src + " (hbm_gbs)",
+                "algorithmic_bytes_per_launch": b, "avg_launch_ms": 1000.0 * t}
 
     top = one(*entries[0])
     top["others"] = [one(*e) for e in entries[1:]]
