@@ -320,6 +320,8 @@ GraphView nd_view(const nd_graph* g) {
     v.tri_e = (const int32_t*)g->tri_e.p;
     v.tri_pos = (const int32_t*)g->tri_pos.p;
     v.n3 = g->n3;
+    v.hoff = (const int64_t*)g->hoff.p;
+    v.htab = (const NdHashSlot*)g->htab.p;
     return v;
 }
 
@@ -650,14 +652,14 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
         hstage = g->edge_mindeg;
         hslices = nd_peel_heavy_slices();
     }
-    DBuf ctl, A0, A1, N0, N1, L0, L1, H, rs, rl, rt, etr, hsc, abits, hoff, htab, hpos;
+    DBuf ctl, A0, A1, N0, N1, L0, L1, H, rs, rl, rt, etr, hsc, abits;
     if ((rc = nd_alloc(c, ctl, sizeof(PeelCtl))) || (rc = nd_alloc(c, A0, 4 * cap)) || (rc = nd_alloc(c, A1, 4 * cap)) ||
         (rc = nd_alloc(c, N0, 4 * cap)) || (rc = nd_alloc(c, N1, 4 * cap)) || (rc = nd_alloc(c, L0, 4 * cap)) ||
         (rc = nd_alloc(c, L1, 4 * cap)) || (rc = nd_alloc(c, H, 4 * hcap)) || (rc = nd_alloc(c, rs, 8 * rcap)) ||
         (rc = nd_alloc(c, rl, 8 * rcap)) || (rc = nd_alloc(c, rt, 8 * rcap)) || (r == 3 && (rc = nd_alloc(c, etr, 4 * std::max<int64_t>(3 * g->n3, 1)))) ||
         (staged && (rc = nd_alloc(c, hsc, 4 * 5 * (hstage + 1) * hslices))) ||
         (rc = nd_alloc(c, abits, r == 3 ? 4 * ((cap + 31) / 32) : 4))) {
-        for (DBuf* b : {&ctl, &A0, &A1, &N0, &N1, &L0, &L1, &H, &rs, &rl, &rt, &etr, &hsc, &abits, &hoff, &htab, &hpos}) nd_free(c, *b);
+        for (DBuf* b : {&ctl, &A0, &A1, &N0, &N1, &L0, &L1, &H, &rs, &rl, &rt, &etr, &hsc, &abits}) nd_free(c, *b);
         return rc;
     }
     PeelView<CT> P;
@@ -696,15 +698,11 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
     P.hoff = nullptr;
     P.htab = nullptr;
     P.hpos = nullptr;
-    if (r == 3 && (rc = build_tri_hash(g, hoff, htab, hpos))) {
-        for (DBuf* b : {&ctl, &A0, &A1, &N0, &N1, &L0, &L1, &H, &rs, &rl, &rt, &etr, &hsc, &abits, &hoff, &htab, &hpos})
-            nd_free(c, *b);
-        return rc;
-    }
     if (r == 3) {
-        P.hoff = (const int64_t*)hoff.p;
-        P.htab = (NdHashSlot*)htab.p;
-        P.hpos = (const int32_t*)hpos.p;
+        // the hash directory, when the decomposition built one (nd_decompose_dev, (3,4))
+        P.hoff = (const int64_t*)g->hoff.p;
+        P.htab = (NdHashSlot*)g->htab.p;
+        P.hpos = (const int32_t*)g->hpos.p;
         P.et_rnd = (int32_t*)etr.p;
         P.tri_e = (const int32_t*)g->tri_e.p;
         P.tri_pos = (const int32_t*)g->tri_pos.p;
@@ -833,7 +831,7 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
             rc = nd_sync(c, "peel record");
         }
     }
-    for (DBuf* b : {&ctl, &A0, &A1, &N0, &N1, &L0, &L1, &H, &rs, &rl, &rt, &etr, &hsc, &abits, &hoff, &htab, &hpos}) nd_free(c, *b);
+    for (DBuf* b : {&ctl, &A0, &A1, &N0, &N1, &L0, &L1, &H, &rs, &rl, &rt, &etr, &hsc, &abits}) nd_free(c, *b);
     return rc;
 }
 
@@ -855,6 +853,9 @@ int nd_decompose_dev(nd_graph* g, int r, int s, int count_width, int flags, Peel
     int rc = nd_alloc(c, po.core, 4 * std::max<int64_t>(n_r, 1));
     if (!rc) rc = nd_alloc(c, po.rnd, 4 * std::max<int64_t>(n_r, 1));
     cudaEventRecord(e0, c->stream);
+    // (3,4): the hash directory of the long triangle lists serves the count's searches and the
+    // peel's lookups; it is built inside the counting interval and freed with the decomposition
+    if (!rc && r == 3 && s == 4) rc = build_tri_hash(g, g->hoff, g->htab, g->hpos);
     if (!rc) rc = nd_count_into(g, r, s, w, n_r, cnt);
     cudaEventRecord(e1, c->stream);
     unsigned long long tot = 0;
@@ -873,6 +874,7 @@ int nd_decompose_dev(nd_graph* g, int r, int s, int count_width, int flags, Peel
     cudaEventDestroy(e2);
     cudaEventDestroy(e3);
     nd_free(c, cnt);
+    for (DBuf* b : {&g->hoff, &g->htab, &g->hpos}) nd_free(c, *b);
     if (rc) return rc;
     S.n_r = n_r;
     S.n_s = (int64_t)(tot / (unsigned long long)binom64(s, r));

@@ -208,6 +208,9 @@ struct GraphView {
     const int32_t* tri_e;
     const int32_t* tri_pos;
     int64_t n3;
+    // hash directory of the long triangle lists (during a (3,4) decomposition), else NULL
+    const int64_t* hoff;
+    const NdHashSlot* htab;
 };
 
 // Control block of the device-resident peeling loop (one per decomposition).

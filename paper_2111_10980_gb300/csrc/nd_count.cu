@@ -79,18 +79,27 @@ __global__ void k_count34(GraphView g, CT* __restrict__ cnt) {
         // the two shortest lists: (b0, n0) drives, (b1, n1) is searched
         if (n1 < n0) {
             int64_t tb = b0, tn = n0;
-            b0 = b1, n0 = n1, b1 = tb, n1 = tn;
+            int32_t te = e0;
+            b0 = b1, n0 = n1, e0 = e1, b1 = tb, n1 = tn, e1 = te;
         }
         if (n2 < n0) {
             int64_t tb = b0, tn = n0;
-            b0 = b2, n0 = n2, b2 = tb, n2 = tn;
+            int32_t te = e0;
+            b0 = b2, n0 = n2, e0 = e2, b2 = tb, n2 = tn, e2 = te;
         }
-        if (n2 < n1) b1 = b2, n1 = n2;
+        if (n2 < n1) b1 = b2, n1 = n2, e1 = e2;
         int c = 0;
-        if (nd_prefer_merge(n0, n1))
+        if (nd_prefer_merge(n0, n1)) {
             nd_warp_merge(g.et_w + b0, n0, g.et_w + b1, n1, [&](bool f, int64_t, int64_t) { c += f ? 1 : 0; });
-        else
+        } else if (g.htab && nd_hashed(n1)) {
+            // the long list has a hash directory: one probe instead of a bisection
+            const NdHashSlot* tab = g.htab + g.hoff[e1];
+            int k = nd_hash_bits(n1);
+            int32_t id, rnd;
+            for (int64_t i = lane; i < n0; i += 32) c += nd_hash_find(tab, k, g.et_w[b0 + i], id, rnd) ? 1 : 0;
+        } else {
             for (int64_t i = lane; i < n0; i += 32) c += nd_find(g.et_w + b1, n1, g.et_w[b0 + i]) >= 0 ? 1 : 0;
+        }
         c = warp_sum(c);
         if (lane == 0) cnt[t] = (CT)c;
     }

@@ -312,15 +312,18 @@ __global__ void k_tri_hash_fill(GraphView g, const int64_t* __restrict__ hoff, N
         int k = nd_hash_bits(n);
         uint32_t mask = (1u << k) - 1u;
         NdHashSlot* t = tab + hoff[e];
+        const int32_t a = g.eu[e], c = g.ev[e];  // e = (a, c), a < c
         for (int64_t p = lane; p < n; p += 32) {
             int32_t w = g.et_w[b + p], id = g.et_t[b + p];
+            // the triangle's edges are (xy, xz, yz) for x < y < z: e is xy when w > c, xz when
+            // a < w < c, yz when w < a
+            int x = w > c ? 0 : (w > a ? 1 : 2);
             unsigned long long key = ((unsigned long long)(uint32_t)id << 32) | (uint32_t)w;  // little endian: w first
             uint32_t s = nd_hash_slot(w, k);
             for (uint32_t probes = 0; probes <= mask; ++probes) {
                 unsigned long long* half = reinterpret_cast<unsigned long long*>(t + s);
                 if (atomicCAS(half, 0xffffffffffffffffull, key) == 0xffffffffffffffffull) {
                     t[s].rnd = ND_UNPEELED;
-                    int x = g.tri_e[3 * (int64_t)id] == e ? 0 : (g.tri_e[3 * (int64_t)id + 1] == e ? 1 : 2);
                     hpos[3 * (int64_t)id + x] = (int32_t)s;
                     break;
                 }

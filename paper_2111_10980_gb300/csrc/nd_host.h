@@ -48,6 +48,8 @@ struct nd_graph {
     bool have_tri = false;
     int64_t n3 = 0;
     DBuf et_rp, et_w, et_t, tbase, tri_e, tri_pos;
+    // hash directory of the long triangle lists, held only while a (3,4) decomposition runs
+    DBuf hoff, htab, hpos;
     // record of the last decomposition
     bool have_last = false;
     int64_t last_rho = 0;
