@@ -201,3 +201,25 @@ def test_errors_are_reported(nd, ctx):
         nd.nd_load_csr(small, gg.complete(60).rowptr, gg.complete(60).col)
     assert ei.value.code == nd.ND_ENOMEM
     nd.nd_ctx_destroy(small)
+
+
+def test_phase_and_round_times(nd, ctx):
+    """The persistent kernel's timing record: per-phase times add up to at most the peel's time,
+    the per-round Update times add up to the Update phases, and every round is accounted for."""
+    g = gg.rmat(12, 16, 0.57, 0.19, 0.19, seed=5)
+    G = nd.nd_load_csr(ctx, g.rowptr, g.col)
+    try:
+        for r, s in [(2, 3), (3, 4)]:
+            _, _, st = nd.nd_decompose(G, r, s, flags=nd.ND_PEEL_PERSISTENT)
+            ph = st["t_phase_ms"]
+            assert len(ph) == 6 and min(ph) >= 0.0
+            assert 0.0 < sum(ph) <= st["t_peel_ms"] * 1.05
+            sizes, _, rho = nd.nd_rounds(G)
+            ns = nd.nd_round_times(G)
+            assert ns.size == rho == sizes.size
+            assert (ns >= 0).all()
+            assert abs(ns.sum() / 1e6 - (ph[4] + ph[5])) <= 1e-3 * max(1.0, ph[4] + ph[5]) + 1e-3
+            _, _, st = nd.nd_decompose(G, r, s, flags=nd.ND_NO_GRAPH)
+            assert sum(st["t_phase_ms"]) == 0.0 and not nd.nd_round_times(G).any()
+    finally:
+        nd.nd_graph_free(G)
