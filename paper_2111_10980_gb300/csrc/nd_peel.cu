@@ -542,6 +542,12 @@ __device__ __forceinline__ void after_dec(const RoundEnv<CT>& E, int32_t x, int6
 }
 
 
+// Whether a member of a destroyed S with round tag r has its count decremented on the device: not
+// if it is in A (r = t), and not if it was already pushed into the next round's A during this
+// round (r = t + 1): its core number is fixed and its count is never read again (every later
+// reader of counts takes unpeeled r-cliques only). Both still count as decrements of Algorithm 2.
+__device__ __forceinline__ bool dec_live(int32_t r, int32_t t) { return r != t && r != t + 1; }
+
 // Update-Func for the s-clique S made of R and the other r-subsets o[0..M). Returns whether S
 // was live (no r-subset peeled in an earlier round).
 template <typename CT, int M>
@@ -559,13 +565,12 @@ __device__ __forceinline__ void update_func(const RoundEnv<CT>& E, int32_t R, co
     // issue every decrement before looking at any result (the atomics overlap in flight)
     int64_t old[M];
 #pragma unroll
-    for (int i = 0; i < M; ++i) old[i] = ro[i] != E.t ? nd_atomic_dec(&E.P.cnt[o[i]]) : 0;
+    for (int i = 0; i < M; ++i) old[i] = dec_live(ro[i], E.t) ? nd_atomic_dec(&E.P.cnt[o[i]]) : 0;
 #pragma unroll
-    for (int i = 0; i < M; ++i)
-        if (ro[i] != E.t) {
-            k.decs++;
-            after_dec(E, o[i], old[i]);
-        }
+    for (int i = 0; i < M; ++i) {
+        k.decs += ro[i] != E.t;
+        if (dec_live(ro[i], E.t)) after_dec(E, o[i], old[i]);
+    }
 }
 
 __device__ __forceinline__ void add_counters(PeelCtl* c, UpdCounters k) {
@@ -916,13 +921,13 @@ struct Upd34 {
         if (!look(g, E, q, 2, w, id2, r2) || r2 < E.t || (r2 == E.t && id2 < R)) return;
         k.listed++;
         // issue the decrements before looking at any result (the atomics overlap in flight)
-        int64_t o0 = r0 != E.t ? nd_atomic_dec(&E.P.cnt[id0]) : 0;
-        int64_t o1 = r1 != E.t ? nd_atomic_dec(&E.P.cnt[id1]) : 0;
-        int64_t o2 = r2 != E.t ? nd_atomic_dec(&E.P.cnt[id2]) : 0;
+        int64_t o0 = dec_live(r0, E.t) ? nd_atomic_dec(&E.P.cnt[id0]) : 0;
+        int64_t o1 = dec_live(r1, E.t) ? nd_atomic_dec(&E.P.cnt[id1]) : 0;
+        int64_t o2 = dec_live(r2, E.t) ? nd_atomic_dec(&E.P.cnt[id2]) : 0;
         k.decs += (r0 != E.t) + (r1 != E.t) + (r2 != E.t);
-        if (r0 != E.t) after_dec(E, id0, o0);
-        if (r1 != E.t) after_dec(E, id1, o1);
-        if (r2 != E.t) after_dec(E, id2, o2);
+        if (dec_live(r0, E.t)) after_dec(E, id0, o0);
+        if (dec_live(r1, E.t)) after_dec(E, id1, o1);
+        if (dec_live(r2, E.t)) after_dec(E, id2, o2);
     }
 
     // Both search lists hashed: candidates j and j + 32 of this lane at once, each step issuing
@@ -965,25 +970,25 @@ struct Upd34 {
         la = la && ra1 >= E.t && !(ra1 == E.t && ia1 < R) && ra2 >= E.t && !(ra2 == E.t && ia2 < R);
         lb = lb && rb1 >= E.t && !(rb1 == E.t && ib1 < R) && rb2 >= E.t && !(rb2 == E.t && ib2 < R);
         // decrements of both 4-cliques go out before any result is looked at
-        int64_t oa0 = la && ra != E.t ? nd_atomic_dec(&E.P.cnt[ia]) : 0;
-        int64_t oa1 = la && ra1 != E.t ? nd_atomic_dec(&E.P.cnt[ia1]) : 0;
-        int64_t oa2 = la && ra2 != E.t ? nd_atomic_dec(&E.P.cnt[ia2]) : 0;
-        int64_t ob0 = lb && rb != E.t ? nd_atomic_dec(&E.P.cnt[ib]) : 0;
-        int64_t ob1 = lb && rb1 != E.t ? nd_atomic_dec(&E.P.cnt[ib1]) : 0;
-        int64_t ob2 = lb && rb2 != E.t ? nd_atomic_dec(&E.P.cnt[ib2]) : 0;
+        int64_t oa0 = la && dec_live(ra, E.t) ? nd_atomic_dec(&E.P.cnt[ia]) : 0;
+        int64_t oa1 = la && dec_live(ra1, E.t) ? nd_atomic_dec(&E.P.cnt[ia1]) : 0;
+        int64_t oa2 = la && dec_live(ra2, E.t) ? nd_atomic_dec(&E.P.cnt[ia2]) : 0;
+        int64_t ob0 = lb && dec_live(rb, E.t) ? nd_atomic_dec(&E.P.cnt[ib]) : 0;
+        int64_t ob1 = lb && dec_live(rb1, E.t) ? nd_atomic_dec(&E.P.cnt[ib1]) : 0;
+        int64_t ob2 = lb && dec_live(rb2, E.t) ? nd_atomic_dec(&E.P.cnt[ib2]) : 0;
         if (la) {
             k.listed++;
             k.decs += (ra != E.t) + (ra1 != E.t) + (ra2 != E.t);
-            if (ra != E.t) after_dec(E, ia, oa0);
-            if (ra1 != E.t) after_dec(E, ia1, oa1);
-            if (ra2 != E.t) after_dec(E, ia2, oa2);
+            if (dec_live(ra, E.t)) after_dec(E, ia, oa0);
+            if (dec_live(ra1, E.t)) after_dec(E, ia1, oa1);
+            if (dec_live(ra2, E.t)) after_dec(E, ia2, oa2);
         }
         if (lb) {
             k.listed++;
             k.decs += (rb != E.t) + (rb1 != E.t) + (rb2 != E.t);
-            if (rb != E.t) after_dec(E, ib, ob0);
-            if (rb1 != E.t) after_dec(E, ib1, ob1);
-            if (rb2 != E.t) after_dec(E, ib2, ob2);
+            if (dec_live(rb, E.t)) after_dec(E, ib, ob0);
+            if (dec_live(rb1, E.t)) after_dec(E, ib1, ob1);
+            if (dec_live(rb2, E.t)) after_dec(E, ib2, ob2);
         }
     }
 };
