@@ -855,7 +855,14 @@ int nd_decompose_dev(nd_graph* g, int r, int s, int count_width, int flags, Peel
     cudaEventRecord(e0, c->stream);
     // (3,4): the hash directory of the long triangle lists serves the count's searches and the
     // peel's lookups; it is built inside the counting interval and freed with the decomposition
-    if (!rc && r == 3 && s == 4) rc = build_tri_hash(g, g->hoff, g->htab, g->hpos);
+    if (!rc && r == 3 && s == 4) {
+        rc = build_tri_hash(g, g->hoff, g->htab, g->hpos);
+        if (rc == ND_ENOMEM) {
+            // the directory is an accelerator: without room for it the lists are bisected
+            for (DBuf* b : {&g->hoff, &g->htab, &g->hpos}) nd_free(c, *b);
+            rc = ND_OK;
+        }
+    }
     if (!rc) rc = nd_count_into(g, r, s, w, n_r, cnt);
     cudaEventRecord(e1, c->stream);
     unsigned long long tot = 0;

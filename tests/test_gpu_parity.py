@@ -223,3 +223,34 @@ def test_phase_and_round_times(nd, ctx):
             assert sum(st["t_phase_ms"]) == 0.0 and not nd.nd_round_times(G).any()
     finally:
         nd.nd_graph_free(G)
+
+
+def test_34_without_room_for_the_hash_directory(nd):
+    """When the lists' hash directory cannot be allocated (here: an allocator that refuses any
+    block above 16 MB, which only the directory's tables reach), (3,4) runs with bisection and
+    still gives the oracle's result."""
+    import torch
+
+    g = gg.rmat(12, 16, 0.57, 0.19, 0.19, seed=9)
+    want = orc.decompose(g, 3, 4)
+    alloc, free = nd.torch_allocator_hooks(0)
+    refused = []
+
+    def small_only(nbytes, stream):
+        if nbytes > 16 << 20:
+            refused.append(nbytes)
+            return 0
+        return alloc(nbytes, stream)
+
+    stream = torch.cuda.Stream()
+    ctx = nd.nd_ctx_create(0, stream=stream)
+    nd.nd_ctx_set_allocator(ctx, small_only, free)
+    G = nd.nd_load_csr(ctx, g.rowptr, g.col)
+    try:
+        core, rnd, st = nd.nd_decompose(G, 3, 4)
+    finally:
+        nd.nd_graph_free(G)
+        nd.nd_ctx_destroy(ctx)
+    assert refused, "the directory should not have fitted"
+    assert np.array_equal(core, want.core) and np.array_equal(rnd, want.round)
+    assert st["listed"] == want.n_s and st["decrements"] == want.decs
