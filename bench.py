@@ -369,11 +369,11 @@ def main():
 # step), keyed by the fingerprint of the library sources they were taken on; reported as
 # roofline.traffic only while the sources still match.
 NCU_TRAFFIC = {
-    "9e341dbc89f4d9b3": {
-        ("rmat20", "k_peel_loop(3,4)"): 7.649e12,
-        ("rmat20", "k_peel_loop(2,3)"): 115.9e9,
-        ("rmat20", "k_count34"): 1165.0e9,
-        ("rmat20", "k_count23"): 9.63e9,
+    "fcd44b27ffba5a44": {
+        ("rmat20", "k_peel_loop(3,4)"): 7.648e12,
+        ("rmat20", "k_peel_loop(2,3)"): 115.7e9,
+        ("rmat20", "k_count34"): 1164.0e9,
+        ("rmat20", "k_count23"): 9.58e9,
     },
 }
 
