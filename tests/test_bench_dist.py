@@ -71,3 +71,36 @@ def test_units_formula():
     assert bench.units_of(2, 3, 10) == 40
     assert bench.units_of(3, 4, 10) == 50
     assert bench.units_of(2, 4, 1) == 7
+
+
+def _fake_stats(rs_list):
+    st = {}
+    for r, s in rs_list:
+        st[(r, s)] = {"n_r": 1000, "n_s": 5000, "listed": 5000, "decrements": 12000, "count_width": 4,
+                      "t_count_ms": 10.0, "t_peel_ms": 40.0}
+    return [st]
+
+
+def test_roofline_models_and_traffic_gate(monkeypatch):
+    """Every benchmarked (r,s) has a nonzero byte model; the ncu traffic figure is reported only
+    while the library sources match the fingerprint the capture was taken on."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class G:
+        n, m = 100, 400
+
+    for name, rs_list in [("rmat20", [(2, 3), (3, 4)]), ("cl4m", [(3, 4), (2, 4)])]:
+        wl = {"name": name, "rs": rs_list}
+        top = bench.roofline(wl, _fake_stats(rs_list), G())
+        for e in [top] + top["others"]:
+            assert e["algorithmic_bytes_per_launch"] > 0, e["kernel"]
+            assert e["unit"] == "GB/s" and e["bound"] == "hbm"
+    fp = next(iter(bench.NCU_TRAFFIC))
+    wl = {"name": "rmat20", "rs": [(2, 3), (3, 4)]}
+    monkeypatch.setattr(bench, "sources_fingerprint", lambda: fp)
+    top = bench.roofline(wl, _fake_stats(wl["rs"]), G())
+    assert top["traffic"] == bench.NCU_TRAFFIC[fp][("rmat20", top["kernel"])]
+    monkeypatch.setattr(bench, "sources_fingerprint", lambda: "0" * 16)
+    top = bench.roofline(wl, _fake_stats(wl["rs"]), G())
+    assert top["traffic"] is None and all(o["traffic"] is None for o in top["others"])
