@@ -393,8 +393,8 @@ def sources_fingerprint():
 
 def roofline(wl, per_step_stats, g):
     """HBM roofline of the dominant kernel (largest share of the step, from the library's CUDA
-    events on the launching stream), with the algorithmic-byte models stated in the design doc.
-    The other major kernels are reported beside it."""
+    events on the launching stream), with the algorithmic-byte models written out below (lower
+    bounds of what each kernel must move). The other major kernels are reported beside it."""
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))

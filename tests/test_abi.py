@@ -18,9 +18,10 @@ def declared_symbols():
     return names
 
 
-def test_header_declares_the_north_star_calls():
+def test_header_declares_the_hot_path_calls():
     names = declared_symbols()
-    for n in ["nd_load_csr", "nd_orient", "nd_count", "nd_decompose", "nd_ctx_create", "nd_last_error"]:
+    for n in ["nd_load_csr", "nd_orient", "nd_count", "nd_decompose", "nd_ctx_create", "nd_last_error",
+              "nd_rounds", "nd_round_times", "nd_batch_run", "nd_server_create", "nd_submit", "nd_poll"]:
         assert n in names
 
 
