@@ -336,10 +336,14 @@ def main():
                        "peel_mode": args.peel_mode},
             "r_cliques_peeled_per_s": peeled_per_s,
             "wall_s_timed": wall,
-            "per_rs": {f"({r},{s})": {k: stats[(r, s)][k] for k in
-                                      ("n_r", "n_s", "rho", "max_core", "listed", "decrements", "advances", "refills",
-                                       "count_width", "t_orient_ms", "t_index_ms", "t_count_ms", "t_peel_ms",
-                                       "t_total_ms", "t_phase_ms")} for r, s in wl["rs"]},
+            "per_rs": {f"({r},{s})": dict(
+                {k: stats[(r, s)][k] for k in
+                 ("n_r", "n_s", "rho", "max_core", "listed", "decrements", "advances", "refills", "count_width",
+                  "t_orient_ms", "t_index_ms", "t_count_ms", "t_peel_ms", "t_total_ms", "t_phase_ms")},
+                # the count phase alone (s-cliques counted per second) and the peel alone
+                n_s_per_s_count=stats[(r, s)]["n_s"] / max(stats[(r, s)]["t_count_ms"], 1e-9) * 1e3,
+                n_r_per_s_peel=stats[(r, s)]["n_r"] / max(stats[(r, s)]["t_peel_ms"], 1e-9) * 1e3)
+                for r, s in wl["rs"]},
             "gpu_launches": launches,
             "roofline": roof,
             "clocks": clocks}
