@@ -504,17 +504,9 @@ def e2e(nd, wl, g, local, width, steps, world, pg):
 # batched and served workloads
 
 def batch_graphs(count: int, seed: int = 4):
-    """count seeded Chung-Lu graphs: n ~ U[50, 5000], average degree ~ U[8, 40], exponent 2.2,
-    w_0 = min(sqrt(sum w), n - 1); (r,s) uniform over {(1,2), (2,3), (3,4)}."""
-    u = gg.uniform(seed, 3 * count)
-    rs = [(1, 2), (2, 3), (3, 4)]
-    out = []
-    for i in range(count):
-        n = 50 + int(u[3 * i] * 4951)
-        d = 8.0 + u[3 * i + 1] * 32.0
-        g = gg.chung_lu(n, d, 2.2, seed=seed + i, exact=False)
-        out.append((g, rs[min(2, int(u[3 * i + 2] * 3))]))
-    return out
+    """The batched workload: graphgen.batch_workload (Chung-Lu, n ~ U[50, 5000], average degree
+    ~ U[8, 40], exponent 2.2; (r,s) uniform over (1,2), (2,3), (3,4))."""
+    return gg.batch_workload(count, seed)
 
 
 def run_batch(args, nd, world, rank, local, pg):
@@ -575,20 +567,9 @@ def run_batch(args, nd, world, rank, local, pg):
 
 
 def serve_pool(count: int, seed: int = 5):
-    """Graphs of the served stream: Chung-Lu or R-MAT with probability 1/2, edge count
-    log-uniform in [1e2, 1e6]; Chung-Lu with average degree ~U[8, 40], exponent 2.2, n = 2m/d;
-    R-MAT with n = 2^ceil(log2(m/8)) and Graph500 a, b, c."""
-    u = gg.uniform(seed, 3 * count)
-    out = []
-    for i in range(count):
-        m = int(round(math.exp(math.log(1e2) + u[3 * i] * (math.log(1e6) - math.log(1e2)))))
-        if u[3 * i + 1] < 0.5:
-            d = 8.0 + u[3 * i + 2] * 32.0
-            n = max(16, int(2 * m / d))
-            out.append(gg.chung_lu(n, d, 2.2, seed=seed * 100003 + i, exact=False))
-        else:
-            out.append(gg.rmat_m(m, seed=seed * 100003 + i))
-    return out
+    """Graphs of the served stream: graphgen.serve_pool (Chung-Lu or R-MAT, edge count
+    log-uniform in [1e2, 1e6])."""
+    return gg.serve_pool(count, seed)
 
 
 def run_serve(args, nd, world, rank, local, pg):

@@ -314,3 +314,61 @@ def chung_lu_4m_planted(seed: int = 3, n: int = 4_194_304) -> Graph:
     planted communities of 20-60 vertices at internal density 0.7."""
     g = chung_lu(n, 30.0, 2.3, seed=seed, exact=False)
     return with_planted(g, 2000, 20, 60, 0.7, seed + 7919)
+
+
+def batch_workload(count: int, seed: int = 4):
+    """``count`` seeded Chung-Lu graphs with n ~ U[50, 5000], average degree ~ U[8, 40], exponent
+    2.2, w_0 = min(sqrt(sum w), n - 1), each with (r, s) drawn uniformly from (1,2), (2,3), (3,4).
+    Returns a list of (graph, (r, s)); the first k items do not depend on ``count``."""
+    u = uniform(seed, 3 * count)
+    rs = [(1, 2), (2, 3), (3, 4)]
+    out = []
+    for i in range(count):
+        n = 50 + int(u[3 * i] * 4951)
+        d = 8.0 + u[3 * i + 1] * 32.0
+        g = chung_lu(n, d, 2.2, seed=seed + i, exact=False)
+        out.append((g, rs[min(2, int(u[3 * i + 2] * 3))]))
+    return out
+
+
+def serve_pool(count: int, seed: int = 5, max_m: int | None = None):
+    """Graphs of the served stream: Chung-Lu or R-MAT with probability 1/2 each, edge count
+    log-uniform in [1e2, 1e6]; Chung-Lu with average degree ~ U[8, 40], exponent 2.2, n = 2m/d;
+    R-MAT with n = 2^ceil(log2(m/8)) and a, b, c = 0.57, 0.19, 0.19. The first k graphs do not
+    depend on ``count``. With ``max_m``, the draws whose edge count exceeds it are skipped (not
+    generated), the others are the same graphs in the same order."""
+    u = uniform(seed, 3 * count)
+    out = []
+    for i in range(count):
+        m = int(round(math.exp(math.log(1e2) + u[3 * i] * (math.log(1e6) - math.log(1e2)))))
+        if max_m is not None and m > max_m:
+            continue
+        if u[3 * i + 1] < 0.5:
+            d = 8.0 + u[3 * i + 2] * 32.0
+            n = max(16, int(2 * m / d))
+            out.append(chung_lu(n, d, 2.2, seed=seed * 100003 + i, exact=False))
+        else:
+            out.append(rmat_m(m, seed=seed * 100003 + i))
+    return out
+
+
+def hubs_over_sparse(n_common: int = 6000, hubs: int = 4, p_hub: float = 0.9, avg_deg: float = 8.0,
+                     seed: int = 51) -> Graph:
+    """A sparse Chung-Lu graph (exponent 2.2) on ``n_common`` vertices plus ``hubs`` mutually
+    adjacent hub vertices (ids n_common ..), each adjacent to every other vertex with probability
+    p_hub. Hubs reach degree ~ p_hub * n_common, pairs of hubs share ~ p_hub^2 * n_common
+    neighbours and triples ~ p_hub^3 * n_common, so hub vertices, hub edges and hub triangles
+    have neighbour lists of thousands of entries while everything else stays sparse."""
+    base = chung_lu(n_common, avg_deg, 2.2, seed=seed, exact=True)
+    e = base.edges()
+    u = uniform(seed * 7 + 1, hubs * n_common).reshape(hubs, n_common)
+    us, vs = [e[:, 0]], [e[:, 1]]
+    for h in range(hubs):
+        nb = np.nonzero(u[h] < p_hub)[0].astype(np.int32)
+        us.append(np.full(nb.size, n_common + h, np.int32))
+        vs.append(nb)
+        for h2 in range(h + 1, hubs):
+            us.append(np.array([n_common + h], np.int32))
+            vs.append(np.array([n_common + h2], np.int32))
+    return csr_from_edges(n_common + hubs, np.concatenate(us).astype(np.int32), np.concatenate(vs).astype(np.int32),
+                          f"hubs_over_sparse(n={n_common},hubs={hubs},p={p_hub},d={avg_deg},seed={seed})")

@@ -51,7 +51,7 @@ extern "C" {
 #define ND_EINVAL 1     /* bad argument, unsupported (r,s), or malformed CSR (ND_VALIDATE) */
 #define ND_ENOMEM 2     /* device allocation failed or the context's memory budget is exceeded */
 #define ND_EOVERFLOW 3  /* a count exceeds the chosen width, or an id space exceeds int32 */
-#define ND_ETIMEOUT 4   /* the device-side peeling loop hit its round cap */
+#define ND_ETIMEOUT 4   /* the peeling loop hit its round cap, or a bounded device-side wait ran out */
 #define ND_EBUSY 5      /* server has no free slot / request queue full */
 #define ND_PENDING 6    /* nd_poll: the request is still running */
 #define ND_EINTERNAL 7  /* internal inconsistency detected on the device */
@@ -64,6 +64,12 @@ extern "C" {
 #define ND_PEEL_LOOP_GRAPH 0x8  /* nd_decompose: run the peeling loop as one CUDA graph (WHILE/IF nodes) */
 #define ND_PEEL_PERSISTENT 0x10 /* nd_decompose: run the peeling loop as one cooperative kernel (default
                                    when none of these three flags is given and the launch is possible) */
+#define ND_CONTRACT_OFF 0x20    /* nd_decompose (2,3): no graph contraction (Section 5.6) */
+#define ND_CONTRACT_ALWAYS 0x40 /* nd_decompose (2,3): contract before every round, every row that lost an
+                                   entry (exercises the contraction; slower than the default) */
+#define ND_DENSE_BUCKETS 0x80   /* nd_decompose: find each new level with the dense bucket array and its
+                                   doubling search (Section 4.2 Discussion) instead of a scan of the
+                                   bucket window; pays off when the range of counts is small */
 
 /* ---- orientation modes (nd_orient) --------------------------------------------------- */
 #define ND_ORIENT_DEGREE 0     /* rank by (degree, id); out-degree <= sqrt(2m) */
@@ -101,6 +107,10 @@ typedef struct nd_stats {
                             by block 0, barrier waits included: [0] level advance (minimum over the
                             bucket window), [1] window refill, [2] selection of A, [3] id-order
                             rebuild of A, [4] Update, [5] Update of the heavy r-cliques */
+    double t_contract_ms;/* persistent peel kernel only: wall time of the graph contractions (block 0) */
+    int64_t contractions;/* graph contractions run ((2,3), Section 5.6): by default one whenever at least
+                            2n edges were peeled since the previous one, compacting the adjacency rows
+                            that lost at least a quarter of their entries since then */
 } nd_stats;
 
 /* ---- context ------------------------------------------------------------------------- */
@@ -115,6 +125,24 @@ ND_API int nd_ctx_create(int device, void *stream, size_t mem_budget, nd_ctx **o
  * allocator). Must be called before any graph is loaded. Pass NULLs to restore the default
  * (cudaMallocAsync on the context's stream). Errors: ND_EINVAL, ND_EBUSY (graphs exist). */
 ND_API int nd_ctx_set_allocator(nd_ctx *ctx, nd_alloc_fn alloc, nd_free_fn free_fn, void *user);
+
+/* Limits of a context's decompositions (no counterpart in the paper; for callers that bound
+ * the work of one call, and for tests of the failure paths). Each value 0 keeps the default.
+ *   max_rounds          peeling rounds after which nd_decompose gives up with ND_ETIMEOUT
+ *                       (default n_r + 2, which no graph reaches: every round peels >= 1 r-clique)
+ *   barrier_timeout_ns  longest wait of a block of the persistent peel kernel at one grid barrier;
+ *                       a block that waits longer, and every block that sees it gave up, leaves
+ *                       the kernel and nd_decompose returns ND_ETIMEOUT (default 60 s)
+ *   count_limit         largest s-clique count a width-4 count array may hold; a larger count
+ *                       makes nd_count / nd_decompose with count_width 4 return ND_EOVERFLOW
+ *                       (default 2^31 - 1; values above it are clamped to it)
+ *   flags               ND_LIMIT_DROP_BLOCK: the last block of the persistent peel kernel leaves
+ *                       before its first grid barrier, so the other blocks wait for an arrival that
+ *                       never comes until barrier_timeout_ns runs out (a test of that bound)
+ * Applies to calls that start after it returns. Errors: ND_EINVAL (NULL context, negative value). */
+#define ND_LIMIT_DROP_BLOCK 0x1
+ND_API int nd_ctx_set_limits(nd_ctx *ctx, int64_t max_rounds, int64_t barrier_timeout_ns, int64_t count_limit,
+                             int32_t flags);
 
 /* Destroy a context. All graphs created from it must have been freed (ND_EBUSY otherwise). */
 ND_API int nd_ctx_destroy(nd_ctx *ctx);

@@ -16,6 +16,8 @@ Functions (each follows the passage named in its docstring):
 * ``decompose_fixpoint(g, r, s)`` the definition of Section 2 written out as nested fixpoints
 * ``local_counts(g, r, s, tuples)`` per-r-clique s-clique counts one by one (sampled checks)
 * ``certify(...)``              validity + elimination-order certificate of a claimed result
+* ``certify_all(...)``          the same certificate over every r-clique (or a sample), with the
+                                oracle's own id lookups, split across host threads
 """
 from __future__ import annotations
 
@@ -40,7 +42,11 @@ def build_lib(force: bool = False) -> str:
     """Compile the oracle with plain gcc -O2 into ``_liboracle.so``."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-o", tmp, _SRC])
+        base = ["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-o", tmp, _SRC]
+        # OpenMP only splits the certificate's loops across host threads; without it the same
+        # code runs on one thread
+        if subprocess.run(base[:1] + ["-fopenmp"] + base[1:], capture_output=True).returncode != 0:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -68,6 +74,9 @@ def _L():
             lib.orc_certify.restype = ctypes.c_int
             lib.orc_local_counts.argtypes = g3 + [ctypes.c_int, ctypes.c_int, i32p, ctypes.c_int64, i64p]
             lib.orc_local_counts.restype = ctypes.c_int
+            lib.orc_certify_all.argtypes = g3 + [ctypes.c_int, ctypes.c_int, ctypes.c_int64, i32p, i32p, i64p,
+                                                 ctypes.c_int64, i64p, ctypes.c_int64, ctypes.c_int, i64p, i64p, i64p]
+            lib.orc_certify_all.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -193,3 +202,45 @@ def certify(g, r: int, s: int, core: np.ndarray, rnd: np.ndarray, ids: np.ndarra
                             _p(t, ctypes.c_int32), k, cb, None, _p(sv, ctypes.c_int64), _p(so, ctypes.c_int64)),
            "certify")
     return sv[:k], so[:k]
+
+
+def certify_all(g, r: int, s: int, core: np.ndarray, rnd: np.ndarray, levels: np.ndarray, ids=None,
+                nthreads: int = 0) -> dict:
+    """Validity / elimination-order / level certificate of a claimed decomposition (Section 2
+    definition; see ``orc_certify_all``) over every r-clique, or over the r-cliques ``ids``.
+    ``core`` and ``rnd`` cover all n_r r-cliques (canonical order); ``levels[t]`` is the level
+    of round t. Returns the failure counts, the first failing id (-1 if none) and, for a
+    sample, the two supports of each sampled r-clique."""
+    rp, col, a = _g(g)
+    core = np.ascontiguousarray(core, dtype=np.int32)
+    rnd = np.ascontiguousarray(rnd, dtype=np.int32)
+    levels = np.ascontiguousarray(levels, dtype=np.int64)
+    if levels.size == 0:
+        levels = np.zeros(1, np.int64)
+        rho = 0
+    else:
+        rho = levels.size
+    bad = np.zeros(4, np.int64)
+    sv = so = None
+    if ids is None:
+        pids, k = None, 0
+    else:
+        ids = np.ascontiguousarray(ids, dtype=np.int64)
+        k = ids.size
+        pids = _p(ids if k else np.zeros(1, np.int64), ctypes.c_int64)
+        sv = np.zeros(max(k, 1), np.int64)
+        so = np.zeros(max(k, 1), np.int64)
+    rc = _L().orc_certify_all(*a, int(r), int(s), int(core.size), _p(core if core.size else np.zeros(1, np.int32),
+                                                                      ctypes.c_int32),
+                              _p(rnd if rnd.size else np.zeros(1, np.int32), ctypes.c_int32),
+                              _p(levels, ctypes.c_int64), int(rho), pids, int(k), int(nthreads),
+                              _p(bad, ctypes.c_int64), None if sv is None else _p(sv, ctypes.c_int64),
+                              None if so is None else _p(so, ctypes.c_int64))
+    if rc == -3:
+        raise ValueError("certify_all: an r-subset of an s-clique is not an r-clique, or n_r does not match")
+    _check(rc, "certify_all")
+    out = {"bad_valid": int(bad[0]), "bad_order": int(bad[1]), "bad_level": int(bad[2]), "first_bad": int(bad[3])}
+    if sv is not None:
+        out["sup_valid"] = sv[:k]
+        out["sup_order"] = so[:k]
+    return out

@@ -792,3 +792,468 @@ int orc_local_counts(int32_t n, const int64_t *rp, const int32_t *col, int r, in
     for (int d = 0; d <= 8; ++d) free(bufs[d]);
     return rc;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Certificate over every r-clique (or a sample), parallel, for graphs where  */
+/* the peeling loop above is far too slow.                                    */
+/*
+ * What it checks is the same pair of conditions as orc_certify above, which together prove
+ * a claimed (core, round) exact without running Algorithm 2 (Section 2 definition):
+ *   validity:  #{S containing R : every r-subset R' of S has core[R'] >= core[R]} >= core[R];
+ *   order:     #{S containing R : every r-subset R' of S has round[R'] >= round[R]} <= core[R];
+ *   level:     core[R] == levels[round[R]], and levels[] is non-decreasing.
+ * Validity makes {R : core[R] >= c} a set in which every member has support >= c, so the true
+ * core number is at least the claim. For the converse take the true c-nucleus X of any R*;
+ * its first member R0 to be peeled (round t0) still has all of X in rounds >= t0, so the order
+ * count of R0 is at least c, hence levels[t0] = core[R0] >= c, and every member of X (R*
+ * included) is peeled at a level >= levels[t0] >= c.
+ *
+ * Ids are looked up in a trie of ascending tuples built here (level 1: vertices; level j+1:
+ * for each j-clique K with largest vertex x, the vertices w > x adjacent to all of K, in
+ * ascending order). The position of an r-tuple in level r is its rank in the lexicographic
+ * order of all r-cliques, i.e. the canonical id. The s-cliques are listed once each along a
+ * (degree, id) order of the vertices (Section 3, orientation) and sorted before the lookups.
+ * The loops over listing roots and over sampled r-cliques are split across threads (OpenMP
+ * when compiled with it); the arithmetic is the same either way.
+ */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef struct {
+    int r;              /* levels 1..r */
+    int64_t cnt[9];     /* entries per level */
+    int64_t *off[9];    /* off[j][i] .. off[j][i+1]: children (level j+1) of entry i of level j */
+    int32_t *val[9];    /* val[j][i]: the last vertex of entry i of level j */
+} trie;
+
+static void trie_free(trie *T) {
+    for (int j = 0; j <= 8; ++j) {
+        free(T->off[j]);
+        free(T->val[j]);
+    }
+}
+
+/* vertices of entry i of level j (ascending), found by walking up with binary searches */
+static void trie_tuple(const trie *T, int j, int64_t i, int32_t *out) {
+    for (int lv = j; lv >= 1; --lv) {
+        out[lv - 1] = T->val[lv][i];
+        if (lv == 1) break;
+        /* parent = largest p with off[lv-1][p] <= i */
+        int64_t lo = 0, hi = T->cnt[lv - 1];
+        while (hi - lo > 1) {
+            int64_t mid = lo + (hi - lo) / 2;
+            if (T->off[lv - 1][mid] <= i)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        i = lo;
+    }
+}
+
+static int64_t trie_children(const og *g, const int32_t *K, int j, int32_t *out) {
+    /* vertices w > K[j-1] adjacent to all of K[0..j): walk the neighbours above K[j-1] of the
+     * member with the fewest neighbours and test adjacency to the others */
+    int32_t x = K[j - 1], y0 = K[0];
+    for (int y = 1; y < j; ++y)
+        if (deg(g, K[y]) < deg(g, y0)) y0 = K[y];
+    const int32_t *nb = g->col + g->rp[y0];
+    int64_t d = deg(g, y0), c = 0;
+    int64_t lo = 0, hi = d; /* first neighbour of y0 above x */
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (nb[mid] <= x)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    for (int64_t q = lo; q < d; ++q) {
+        int32_t w = nb[q];
+        int all = 1;
+        for (int y = 0; y < j && all; ++y)
+            if (K[y] != y0) all = adjacent(g, K[y], w);
+        if (all) {
+            if (out) out[c] = w;
+            c++;
+        }
+    }
+    return c;
+}
+
+static int trie_build(const og *g, int r, trie *T) {
+    memset(T, 0, sizeof(*T));
+    T->r = r;
+    T->cnt[1] = g->n;
+    T->val[1] = (int32_t *)malloc((size_t)(g->n > 0 ? g->n : 1) * sizeof(int32_t));
+    if (!T->val[1]) return -2;
+    for (int32_t v = 0; v < g->n; ++v) T->val[1][v] = v;
+    for (int j = 1; j < r; ++j) {
+        int64_t nj = T->cnt[j];
+        int64_t *off = (int64_t *)malloc((size_t)(nj + 1) * sizeof(int64_t));
+        if (!off) return -2;
+        T->off[j] = off;
+        int bad = 0;
+#pragma omp parallel for schedule(dynamic, 256)
+        for (int64_t i = 0; i < nj; ++i) {
+            int32_t K[8];
+            trie_tuple(T, j, i, K);
+            off[i + 1] = trie_children(g, K, j, NULL);
+        }
+        off[0] = 0;
+        for (int64_t i = 0; i < nj; ++i) off[i + 1] += off[i];
+        T->cnt[j + 1] = off[nj];
+        T->val[j + 1] = (int32_t *)malloc((size_t)(off[nj] > 0 ? off[nj] : 1) * sizeof(int32_t));
+        if (!T->val[j + 1]) return -2;
+#pragma omp parallel for schedule(dynamic, 256)
+        for (int64_t i = 0; i < nj; ++i) {
+            int32_t K[8];
+            trie_tuple(T, j, i, K);
+            int64_t c = trie_children(g, K, j, T->val[j + 1] + off[i]);
+            if (c != off[i + 1] - off[i]) bad = 1;
+        }
+        if (bad) return -3;
+    }
+    return 0;
+}
+
+/* canonical id of the ascending r-tuple x, or -1 if x is not an r-clique */
+static int64_t trie_find(const trie *T, const int32_t *x) {
+    if (x[0] < 0 || x[0] >= T->cnt[1]) return -1;
+    int64_t i = x[0];
+    for (int j = 1; j < T->r; ++j) {
+        int64_t lo = T->off[j][i], hi = T->off[j][i + 1];
+        const int32_t *a = T->val[j + 1];
+        while (lo < hi) {
+            int64_t mid = lo + (hi - lo) / 2;
+            if (a[mid] < x[j])
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        if (lo >= T->off[j][i + 1] || a[lo] != x[j]) return -1;
+        i = lo;
+    }
+    return i;
+}
+
+typedef struct {
+    const og *g;
+    const trie *T;
+    int r, s;
+    const int32_t *core, *round;
+    int32_t *valid, *order; /* full mode: per r-clique tallies (atomic adds) */
+    int32_t R[8];           /* sample mode: the r-clique being checked */
+    int32_t cR, tR;
+    int64_t v_one, o_one;   /* sample mode tallies */
+    int sample;
+    int bad;
+} fcert;
+
+static void isort(int32_t *a, int n) {
+    for (int i = 1; i < n; ++i)
+        for (int j = i; j > 0 && a[j - 1] > a[j]; --j) {
+            int32_t t = a[j];
+            a[j] = a[j - 1];
+            a[j - 1] = t;
+        }
+}
+
+/* one s-clique S (ascending): look up its r-subsets, then tally */
+static void fcert_s(fcert *K, const int32_t *S) {
+    int64_t ids[128];
+    int32_t sub[8];
+    int k = 0, s = K->s, r = K->r;
+    int32_t mc = INT32_MAX, mr = INT32_MAX;
+    for (unsigned mask = 0; mask < (1u << s); ++mask) {
+        if (__builtin_popcount(mask) != r) continue;
+        int q = 0;
+        for (int b = 0; b < s; ++b)
+            if (mask >> b & 1u) sub[q++] = S[b];
+        int64_t id = trie_find(K->T, sub);
+        if (id < 0) {
+            K->bad = 1;
+            return;
+        }
+        ids[k++] = id;
+        if (K->core[id] < mc) mc = K->core[id];
+        if (K->round[id] < mr) mr = K->round[id];
+    }
+    if (K->sample) {
+        K->v_one += mc >= K->cR;
+        K->o_one += mr >= K->tR;
+        return;
+    }
+    for (int q = 0; q < k; ++q) {
+        if (mc >= K->core[ids[q]]) __atomic_fetch_add(&K->valid[ids[q]], 1, __ATOMIC_RELAXED);
+        if (mr >= K->round[ids[q]]) __atomic_fetch_add(&K->order[ids[q]], 1, __ATOMIC_RELAXED);
+    }
+}
+
+/* full mode: every s-clique once, grown along the (degree, id) order; out-lists dg[] */
+typedef struct {
+    const int64_t *orp;
+    const int32_t *ocol; /* out-neighbours (higher in the order), ascending ids */
+} ograph;
+
+static int64_t sorted_intersect(const int32_t *a, int64_t na, const int32_t *b, int64_t nb, int32_t *out) {
+    int64_t i = 0, j = 0, c = 0;
+    while (i < na && j < nb) {
+        if (a[i] < b[j])
+            ++i;
+        else if (a[i] > b[j])
+            ++j;
+        else {
+            out[c++] = a[i];
+            ++i;
+            ++j;
+        }
+    }
+    return c;
+}
+
+static void fcert_grow(fcert *K, const ograph *D, int32_t *S, int depth, const int32_t *I, int64_t nI,
+                       int32_t **bufs) {
+    if (depth == K->s) {
+        int32_t t[8];
+        memcpy(t, S, (size_t)K->s * sizeof(int32_t));
+        isort(t, K->s);
+        fcert_s(K, t);
+        return;
+    }
+    for (int64_t i = 0; i < nI; ++i) {
+        int32_t v = I[i];
+        S[depth] = v;
+        if (depth + 1 == K->s) {
+            fcert_grow(K, D, S, depth + 1, NULL, 0, bufs);
+            continue;
+        }
+        int64_t nn = sorted_intersect(I, nI, D->ocol + D->orp[v], D->orp[v + 1] - D->orp[v], bufs[depth + 1]);
+        fcert_grow(K, D, S, depth + 1, bufs[depth + 1], nn, bufs);
+    }
+}
+
+/* sample mode: the (s-r)-cliques in I = common neighbourhood of R, ascending growth */
+static void fcert_grow_r(fcert *K, int32_t *Cset, int depth, const int32_t *I, int64_t nI, int32_t **bufs) {
+    int need = K->s - K->r;
+    if (depth == need) {
+        int32_t S[8];
+        int i = 0, j = 0, k = 0, r = K->r;
+        while (i < r || j < need) {
+            if (j >= need || (i < r && K->R[i] < Cset[j]))
+                S[k++] = K->R[i++];
+            else
+                S[k++] = Cset[j++];
+        }
+        fcert_s(K, S);
+        return;
+    }
+    for (int64_t i = 0; i < nI; ++i) {
+        int32_t v = I[i];
+        Cset[depth] = v;
+        if (depth + 1 == need) {
+            fcert_grow_r(K, Cset, depth + 1, NULL, 0, bufs);
+            continue;
+        }
+        int64_t nn = intersect_after(K->g, I, i, nI, v, bufs[depth + 1]);
+        fcert_grow_r(K, Cset, depth + 1, bufs[depth + 1], nn, bufs);
+    }
+}
+
+static int deg_order_less(const og *g, int32_t a, int32_t b) {
+    return deg(g, a) < deg(g, b) || (deg(g, a) == deg(g, b) && a < b);
+}
+
+/* Certificate of a claimed (core, round, levels) over every r-clique (ids == NULL) or over the
+ * r-cliques ids[0..nids). n_r: number of r-cliques the claim covers (checked against the trie).
+ * Outputs (each nullable): bad[0] validity failures, bad[1] order failures, bad[2] level
+ * failures (core != levels[round], round outside [0, rho), or levels decreasing), bad[3] the
+ * first failing id (-1 if none); sample mode also writes sup_valid[q], sup_order[q].
+ * nthreads <= 0 uses the default. Returns 0, -1 (bad r,s), -2 (memory), -3 (a subset of an
+ * s-clique is missing from the trie, or n_r does not match), -4 (r > 6). */
+int orc_certify_all(int32_t n, const int64_t *rp, const int32_t *col, int r, int s, int64_t n_r, const int32_t *core,
+                    const int32_t *round, const int64_t *levels, int64_t rho, const int64_t *ids, int64_t nids,
+                    int nthreads, int64_t *bad, int64_t *sup_valid, int64_t *sup_order) {
+    if (check_rs(r, s)) return -1;
+    if (r > 6) return -4;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    og g = {n, rp, col};
+    trie T;
+    int rc = trie_build(&g, r, &T);
+    if (rc) {
+        trie_free(&T);
+        return rc;
+    }
+    if (T.cnt[r] != n_r) {
+        trie_free(&T);
+        return -3;
+    }
+    int64_t nb[4] = {0, 0, 0, -1};
+    for (int64_t t = 1; t < rho; ++t)
+        if (levels[t] < levels[t - 1]) nb[2]++;
+    int64_t maxd = 0;
+    for (int32_t v = 0; v < n; ++v)
+        if (deg(&g, v) > maxd) maxd = deg(&g, v);
+    int err = 0;
+    if (!ids) {
+        int32_t *valid = (int32_t *)calloc((size_t)(n_r > 0 ? n_r : 1), sizeof(int32_t));
+        int32_t *order = (int32_t *)calloc((size_t)(n_r > 0 ? n_r : 1), sizeof(int32_t));
+        int64_t *orp = (int64_t *)malloc((size_t)(n + 1) * sizeof(int64_t));
+        int32_t *ocol = (int32_t *)malloc((size_t)(rp[n] / 2 > 0 ? rp[n] / 2 : 1) * sizeof(int32_t));
+        if (!valid || !order || !orp || !ocol) err = -2;
+        if (!err) {
+            orp[0] = 0;
+            for (int32_t v = 0; v < n; ++v) {
+                int64_t c = 0;
+                for (int64_t q = rp[v]; q < rp[v + 1]; ++q) c += deg_order_less(&g, v, col[q]);
+                orp[v + 1] = orp[v] + c;
+            }
+            for (int32_t v = 0; v < n; ++v) {
+                int64_t at = orp[v];
+                for (int64_t q = rp[v]; q < rp[v + 1]; ++q)
+                    if (deg_order_less(&g, v, col[q])) ocol[at++] = col[q];
+            }
+            ograph D = {orp, ocol};
+#pragma omp parallel
+            {
+                fcert K;
+                memset(&K, 0, sizeof(K));
+                K.g = &g;
+                K.T = &T;
+                K.r = r;
+                K.s = s;
+                K.core = core;
+                K.round = round;
+                K.valid = valid;
+                K.order = order;
+                int32_t *bufs[9];
+                int ok = 1;
+                for (int d = 0; d <= 8; ++d) {
+                    bufs[d] = (int32_t *)malloc((size_t)(maxd + 1) * sizeof(int32_t));
+                    if (!bufs[d]) ok = 0;
+                }
+                if (!ok) {
+#pragma omp atomic write
+                    err = -2;
+                }
+#pragma omp for schedule(dynamic, 64)
+                for (int32_t v = 0; v < n; ++v) {
+                    if (!ok) continue;
+                    int32_t S[8];
+                    S[0] = v;
+                    if (s == 1) continue;
+                    fcert_grow(&K, &D, S, 1, ocol + orp[v], orp[v + 1] - orp[v], bufs);
+                }
+                if (K.bad) {
+#pragma omp atomic write
+                    err = -3;
+                }
+                for (int d = 0; d <= 8; ++d) free(bufs[d]);
+            }
+            for (int64_t R = 0; R < n_r && !err; ++R) {
+                int f = 0;
+                if (valid[R] < core[R]) {
+                    nb[0]++;
+                    f = 1;
+                }
+                if ((int64_t)order[R] > (int64_t)core[R]) {
+                    nb[1]++;
+                    f = 1;
+                }
+                if (round[R] < 0 || round[R] >= rho || levels[round[R]] != core[R]) {
+                    nb[2]++;
+                    f = 1;
+                }
+                if (f && nb[3] < 0) nb[3] = R;
+            }
+        }
+        free(valid);
+        free(order);
+        free(orp);
+        free(ocol);
+    } else {
+        int64_t first = INT64_MAX;
+        int64_t b0 = 0, b1 = 0, b2 = 0;
+#pragma omp parallel reduction(+ : b0, b1, b2) reduction(min : first)
+        {
+            fcert K;
+            memset(&K, 0, sizeof(K));
+            K.g = &g;
+            K.T = &T;
+            K.r = r;
+            K.s = s;
+            K.core = core;
+            K.round = round;
+            K.sample = 1;
+            int32_t *bufs[9];
+            int ok = 1;
+            for (int d = 0; d <= 8; ++d) {
+                bufs[d] = (int32_t *)malloc((size_t)(maxd + 1) * sizeof(int32_t));
+                if (!bufs[d]) ok = 0;
+            }
+            if (!ok) {
+#pragma omp atomic write
+                err = -2;
+            }
+#pragma omp for schedule(dynamic, 16)
+            for (int64_t q = 0; q < nids; ++q) {
+                if (!ok) continue;
+                int64_t id = ids[q];
+                if (id < 0 || id >= n_r) {
+                    K.bad = 1;
+                    continue;
+                }
+                trie_tuple(&T, r, id, K.R);
+                K.cR = core[id];
+                K.tR = round[id];
+                K.v_one = K.o_one = 0;
+                int32_t v0 = K.R[0];
+                for (int j = 1; j < r; ++j)
+                    if (deg(&g, K.R[j]) < deg(&g, v0)) v0 = K.R[j];
+                int64_t nI = 0;
+                const int32_t *nbv = g.col + g.rp[v0];
+                for (int64_t j = 0; j < deg(&g, v0); ++j) {
+                    int32_t w = nbv[j], all = 1;
+                    for (int x = 0; x < r && all; ++x)
+                        if (K.R[x] == w || !adjacent(&g, K.R[x], w)) all = 0;
+                    if (all) bufs[0][nI++] = w;
+                }
+                int32_t Cset[8];
+                fcert_grow_r(&K, Cset, 0, bufs[0], nI, bufs);
+                if (sup_valid) sup_valid[q] = K.v_one;
+                if (sup_order) sup_order[q] = K.o_one;
+                int f = 0;
+                if (K.v_one < K.cR) {
+                    b0++;
+                    f = 1;
+                }
+                if (K.o_one > K.cR) {
+                    b1++;
+                    f = 1;
+                }
+                if (K.tR < 0 || K.tR >= rho || levels[K.tR] != K.cR) {
+                    b2++;
+                    f = 1;
+                }
+                if (f && id < first) first = id;
+            }
+            if (K.bad) {
+#pragma omp atomic write
+                err = -3;
+            }
+            for (int d = 0; d <= 8; ++d) free(bufs[d]);
+        }
+        nb[0] += b0;
+        nb[1] += b1;
+        nb[2] += b2;
+        nb[3] = first == INT64_MAX ? -1 : first;
+    }
+    trie_free(&T);
+    if (bad)
+        for (int i = 0; i < 4; ++i) bad[i] = nb[i];
+    return err;
+}

@@ -30,13 +30,17 @@ ND_VALIDATE = 0x2
 ND_NO_GRAPH = 0x4
 ND_PEEL_LOOP_GRAPH = 0x8
 ND_PEEL_PERSISTENT = 0x10
+ND_CONTRACT_OFF = 0x20
+ND_CONTRACT_ALWAYS = 0x40
+ND_DENSE_BUCKETS = 0x80
 ND_ORIENT_DEGREE = 0
 ND_ORIENT_DEGENERACY = 1
+ND_LIMIT_DROP_BLOCK = 0x1
 STATUS_NAMES = {0: "ND_OK", 1: "ND_EINVAL", 2: "ND_ENOMEM", 3: "ND_EOVERFLOW", 4: "ND_ETIMEOUT", 5: "ND_EBUSY",
                 6: "ND_PENDING", 7: "ND_EINTERNAL", 8: "ND_ECUDA"}
 
 # every entry point declared in include/nd.h
-API = ["nd_ctx_create", "nd_ctx_set_allocator", "nd_ctx_destroy", "nd_ctx_bytes_in_use", "nd_kernel_launches", "nd_last_error",
+API = ["nd_ctx_create", "nd_ctx_set_allocator", "nd_ctx_set_limits", "nd_ctx_destroy", "nd_ctx_bytes_in_use", "nd_kernel_launches", "nd_last_error",
        "nd_load_csr", "nd_graph_free", "nd_graph_size", "nd_orient", "nd_graph_reset", "nd_count", "nd_decompose",
        "nd_rounds", "nd_round_times", "nd_rcliques", "nd_batch_run", "nd_server_create", "nd_submit", "nd_poll", "nd_server_drain",
        "nd_server_destroy", "nd_kcore_noalloc"]
@@ -55,7 +59,8 @@ class nd_stats(ctypes.Structure):
                 ("refills", ctypes.c_int64), ("count_width", ctypes.c_int32), ("orient_mode", ctypes.c_int32),
                 ("t_orient_ms", ctypes.c_double), ("t_index_ms", ctypes.c_double), ("t_count_ms", ctypes.c_double),
                 ("t_peel_ms", ctypes.c_double), ("t_total_ms", ctypes.c_double), ("decrements", ctypes.c_int64),
-                ("t_phase_ms", ctypes.c_double * 6)]
+                ("t_phase_ms", ctypes.c_double * 6), ("t_contract_ms", ctypes.c_double),
+                ("contractions", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -113,6 +118,7 @@ def lib() -> ctypes.CDLL:
             ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)
         L.nd_ctx_create.argtypes = [ctypes.c_int, vp, ctypes.c_size_t, ctypes.POINTER(vp)]
         L.nd_ctx_set_allocator.argtypes = [vp, ALLOC_FN, FREE_FN, vp]
+        L.nd_ctx_set_limits.argtypes = [vp, i64, i64, i64, i32]
         L.nd_ctx_destroy.argtypes = [vp]
         L.nd_ctx_bytes_in_use.argtypes = [vp]
         L.nd_ctx_bytes_in_use.restype = ctypes.c_size_t
@@ -208,6 +214,13 @@ def nd_ctx_set_allocator(ctx: Handle, alloc, free):
     f = FREE_FN(lambda p, nbytes, stream, user: free(int(p), int(nbytes), stream))
     _check(lib().nd_ctx_set_allocator(ctx.ptr, a, f, None))
     ctx.hooks = (a, f)  # keep the trampolines alive
+
+
+def nd_ctx_set_limits(ctx: Handle, max_rounds: int = 0, barrier_timeout_ns: int = 0, count_limit: int = 0,
+                      flags: int = 0):
+    """Round cap, grid-barrier wait bound, width-4 count limit and test flags of a context
+    (nd.h: nd_ctx_set_limits); 0 keeps each default."""
+    _check(lib().nd_ctx_set_limits(ctx.ptr, int(max_rounds), int(barrier_timeout_ns), int(count_limit), int(flags)))
 
 
 def torch_allocator_hooks(device: int = 0):

@@ -48,12 +48,25 @@ def _stale(target: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose_ptxas: bool = False, quiet: bool = True) -> str:
-    os.makedirs(BUILD, exist_ok=True)
-    nvcc = _nvcc()
+def _common(verbose_ptxas: bool = False) -> list[str]:
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden", "-I", INCLUDE, "-I", CSRC]
     if verbose_ptxas:
         common += ["-Xptxas", "-v"]
+    return common
+
+
+def commands() -> list[list[str]]:
+    """The nvcc command lines of a full build: one compile per source, then the link."""
+    objs = [os.path.join(BUILD, os.path.basename(src)[:-3] + ".o") for src in sources()]
+    cmds = [["nvcc"] + _common() + ["-c", src, "-o", obj] for src, obj in zip(sources(), objs)]
+    cmds.append(["nvcc"] + ARCH + ["-shared", "-o", LIB] + objs + ["-lcudart"])
+    return cmds
+
+
+def build(force: bool = False, verbose_ptxas: bool = False, quiet: bool = True) -> str:
+    os.makedirs(BUILD, exist_ok=True)
+    nvcc = _nvcc()
+    common = _common(verbose_ptxas)
     hdrs = _headers()
     jobs = []
     objs = []

@@ -170,6 +170,18 @@ extern "C" int nd_ctx_set_allocator(nd_ctx* ctx, nd_alloc_fn alloc, nd_free_fn f
     return ND_OK;
 }
 
+extern "C" int nd_ctx_set_limits(nd_ctx* ctx, int64_t max_rounds, int64_t barrier_timeout_ns, int64_t count_limit,
+                                 int32_t flags) {
+    if (!ctx) return nd_set_error(ND_EINVAL, "nd_ctx_set_limits: NULL context");
+    if (max_rounds < 0 || barrier_timeout_ns < 0 || count_limit < 0 || (flags & ~ND_LIMIT_DROP_BLOCK))
+        return nd_set_error(ND_EINVAL, "nd_ctx_set_limits: negative limit or unknown flag");
+    ctx->max_rounds = max_rounds;
+    ctx->barrier_ns = barrier_timeout_ns;
+    ctx->count_limit = count_limit;
+    ctx->limit_flags = flags;
+    return ND_OK;
+}
+
 extern "C" int nd_ctx_destroy(nd_ctx* ctx) {
     if (!ctx) return ND_OK;
     if (ctx->ngraphs.load() > 0) return nd_set_error(ND_EBUSY, "nd_ctx_destroy: graphs are still loaded");
@@ -520,6 +532,11 @@ int nd_prepare(nd_graph* g, int r, int s, int64_t* n_r, double* t_orient, double
 // the common neighbours of R, at most C(maxdeg, s-r) of them.
 static int64_t count_bound(const nd_graph* g, int r, int s) { return binom64(g->maxdeg, s - r); }
 
+// Largest count a width-4 count array may hold (nd_ctx_set_limits; INT32_MAX by default).
+static int64_t width4_limit(const nd_ctx* c) {
+    return (c->count_limit > 0 && c->count_limit < INT32_MAX) ? c->count_limit : INT32_MAX;
+}
+
 // Runs the counting kernels into a fresh buffer of width w (4 or 8); *cnt receives it.
 int nd_count_into(nd_graph* g, int r, int s, int w, int64_t n_r, DBuf& cnt) {
     nd_ctx* c = g->ctx;
@@ -530,7 +547,8 @@ int nd_count_into(nd_graph* g, int r, int s, int w, int64_t n_r, DBuf& cnt) {
         nd_count_launch<int64_t>(v, r, s, (int64_t*)cnt.p, n_r, st);
         return nd_check_launch("count");
     }
-    if (count_bound(g, r, s) <= INT32_MAX) {
+    int64_t limit = width4_limit(c);
+    if (count_bound(g, r, s) <= limit) {
         nd_count_launch<int32_t>(v, r, s, (int32_t*)cnt.p, n_r, st);
         return nd_check_launch("count");
     }
@@ -539,20 +557,21 @@ int nd_count_into(nd_graph* g, int r, int s, int w, int64_t n_r, DBuf& cnt) {
     ND_TRY(nd_alloc(c, wide, 8 * std::max<int64_t>(n_r, 1)));
     nd_count_launch<int64_t>(v, r, s, (int64_t*)wide.p, n_r, st);
     scalar_zero(g);
-    nd_narrow_i64((const int64_t*)wide.p, (int32_t*)cnt.p, n_r, (int*)g->scal.p, st);
+    nd_narrow_i64((const int64_t*)wide.p, (int32_t*)cnt.p, n_r, limit, (int*)g->scal.p, st);
     int err = 0;
     int rc = nd_check_launch("count");
     if (!rc) rc = read_back(g, g->scal.p, &err, "count");
     nd_free(c, wide);
     if (rc) return rc;
-    if (err) return nd_set_error(ND_EOVERFLOW, "an s-clique count exceeds 2^31-1; use count_width 8");
+    if (err) return nd_set_error(ND_EOVERFLOW, "an s-clique count exceeds %lld, the width-4 limit; use count_width 8",
+                                 (long long)limit);
     return ND_OK;
 }
 
 int nd_pick_width(const nd_graph* g, int r, int s, int count_width, int* w) {
     if (count_width != 0 && count_width != 4 && count_width != 8)
         return nd_set_error(ND_EINVAL, "count_width must be 0, 4 or 8");
-    *w = count_width ? count_width : (count_bound(g, r, s) <= INT32_MAX ? 4 : 8);
+    *w = count_width ? count_width : (count_bound(g, r, s) <= width4_limit(g->ctx) ? 4 : 8);
     return ND_OK;
 }
 
@@ -652,14 +671,37 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
         hstage = g->edge_mindeg;
         hslices = nd_peel_heavy_slices();
     }
-    DBuf ctl, A0, A1, N0, N1, L0, L1, H, rs, rl, rt, etr, hsc, abits;
+    // (2,3) graph contraction (Section 5.6): compacted copies of the rows and their lengths
+    bool contract = r == 2 && s == 3 && !(flags & ND_CONTRACT_OFF);
+    // dense buckets (Section 4.2 Discussion): one bucket per count value up to the largest count
+    bool dense = flags & ND_DENSE_BUCKETS;
+    int64_t bmax = 0;
+    if (dense) {
+        unsigned long long mx = 0;
+        ND_TRY(scalar_zero(g));
+        if (sizeof(CT) == 8)
+            nd_max_i64((const int64_t*)cnt.p, n_r, (unsigned long long*)g->scal.p, st);
+        else
+            nd_max_i32((const int32_t*)cnt.p, n_r, (unsigned long long*)g->scal.p, st);
+        ND_TRY(nd_check_launch("peel setup"));
+        ND_TRY(read_back(g, g->scal.p, &mx, "peel setup"));
+        bmax = (int64_t)mx + 1;
+    }
+    DBuf ctl, A0, A1, N0, N1, L0, L1, H, rs, rl, rt, etr, hsc, abits, ccol, cpos, clen, cprev, bcnt;
     if ((rc = nd_alloc(c, ctl, sizeof(PeelCtl))) || (rc = nd_alloc(c, A0, 4 * cap)) || (rc = nd_alloc(c, A1, 4 * cap)) ||
         (rc = nd_alloc(c, N0, 4 * cap)) || (rc = nd_alloc(c, N1, 4 * cap)) || (rc = nd_alloc(c, L0, 4 * cap)) ||
         (rc = nd_alloc(c, L1, 4 * cap)) || (rc = nd_alloc(c, H, 4 * hcap)) || (rc = nd_alloc(c, rs, 8 * rcap)) ||
         (rc = nd_alloc(c, rl, 8 * rcap)) || (rc = nd_alloc(c, rt, 8 * rcap)) || (r == 3 && (rc = nd_alloc(c, etr, 4 * std::max<int64_t>(3 * g->n3, 1)))) ||
         (staged && (rc = nd_alloc(c, hsc, 4 * 5 * (hstage + 1) * hslices))) ||
-        (rc = nd_alloc(c, abits, r == 3 ? 4 * ((cap + 31) / 32) : 4))) {
-        for (DBuf* b : {&ctl, &A0, &A1, &N0, &N1, &L0, &L1, &H, &rs, &rl, &rt, &etr, &hsc, &abits}) nd_free(c, *b);
+        (rc = nd_alloc(c, abits, r == 3 ? 4 * ((cap + 31) / 32) : 4)) ||
+        (contract && ((rc = nd_alloc(c, ccol, 4 * std::max<int64_t>(g->nnz, 1))) ||
+                      (rc = nd_alloc(c, cpos, 4 * std::max<int64_t>(g->nnz, 1))) ||
+                      (rc = nd_alloc(c, clen, 4 * std::max<int64_t>(g->n, 1))) ||
+                      (rc = nd_alloc(c, cprev, 4 * std::max<int64_t>(g->n, 1))))) ||
+        (dense && (rc = nd_alloc(c, bcnt, 4 * std::max<int64_t>(bmax, 1))))) {
+        for (DBuf* b : {&ctl, &A0, &A1, &N0, &N1, &L0, &L1, &H, &rs, &rl, &rt, &etr, &hsc, &abits, &ccol, &cpos, &clen,
+                        &cprev, &bcnt})
+            nd_free(c, *b);
         return rc;
     }
     PeelView<CT> P;
@@ -711,8 +753,40 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
     }
     nd_fill_i32(P.rnd, ND_UNPEELED, n_r, st);
     nd_fill_i32(P.core, 0, n_r, st);
-    nd_peel_init(P.ctl, n_r, n_r + 2, st);
+    int64_t max_rounds = c->max_rounds > 0 ? std::min<int64_t>(c->max_rounds, n_r + 2) : n_r + 2;
     GraphView v = nd_view(g);
+    P.ccol = P.cpos = P.clen = P.cprev = nullptr;
+    P.bcnt = nullptr;
+    P.bmax = 0;
+    if (dense) {
+        P.bcnt = (unsigned int*)bcnt.p;
+        P.bmax = bmax;
+        cudaMemsetAsync(bcnt.p, 0, bcnt.bytes, st);  // a failure surfaces at the launch check below
+        nd_bucket_fill<CT>((const CT*)cnt.p, n_r, P.bcnt, bmax, st);
+    }
+    int64_t contract_every = 0;
+    int contract_shift = 2;
+    if (contract) {
+        // the paper's schedule: after at least 2n peeled edges, rows that lost a quarter of their
+        // entries; ND_CONTRACT_ALWAYS: before every round, every row that lost an entry
+        P.ccol = (int32_t*)ccol.p;
+        P.cpos = (int32_t*)cpos.p;
+        P.clen = (int32_t*)clen.p;
+        P.cprev = (int32_t*)cprev.p;
+        if (g->nnz) {
+            cudaMemcpyAsync(P.ccol, g->col.p, 4 * g->nnz, cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync(P.cpos, g->pos2e.p, 4 * g->nnz, cudaMemcpyDeviceToDevice, st);
+        }
+        nd_row_len((const int64_t*)g->rp.p, g->n, P.clen, P.cprev, st);
+        v.col = P.ccol;
+        v.pos2e = P.cpos;
+        v.rlen = P.clen;
+        bool always = flags & ND_CONTRACT_ALWAYS;
+        contract_every = always ? 1 : std::max<int64_t>(2 * (int64_t)g->n, 1);
+        contract_shift = always ? 0 : 2;
+    }
+    nd_peel_init(P.ctl, n_r, max_rounds, st, (uint64_t)c->barrier_ns, (c->limit_flags & ND_LIMIT_DROP_BLOCK) ? 1 : 0,
+                 contract_every, contract_shift);
     bool looped = false;
     int persistent_launches = 0;
     bool want_persistent = (flags & ND_PEEL_PERSISTENT) || !(flags & (ND_NO_GRAPH | ND_PEEL_LOOP_GRAPH));
@@ -809,11 +883,12 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
             po.rho = h.t;
             po.max_core = n_r ? h.k : 0;
             if (looped && !persistent_launches)  // graph nodes executed: every iteration (rho + 1), plus advance and refill phases
-                nd_note_launches((int64_t)(h.t + 1) * nd_peel_nodes_per_round(r, s) + 3 * (int64_t)h.advances +
-                                 4 * (int64_t)h.refills);
+                nd_note_launches((int64_t)(h.t + 1) * nd_peel_nodes_per_round(r, s, contract) +
+                                 3 * (int64_t)h.advances + 4 * (int64_t)h.refills);
             po.listed = (int64_t)h.listed;
             po.decs = (int64_t)h.decs;
-            for (int i = 0; i < 6; ++i) po.phase_ms[i] = persistent_launches ? 1e-6 * (double)h.ph_ns[i] : 0.0;
+            for (int i = 0; i < 7; ++i) po.phase_ms[i] = persistent_launches ? 1e-6 * (double)h.ph_ns[i] : 0.0;
+            po.contractions = h.contractions;
             po.advances = h.advances;
             po.refills = h.refills;
             if (h.k > INT32_MAX && !rc) rc = nd_set_error(ND_EOVERFLOW, "a core number exceeds 2^31-1");
@@ -831,7 +906,9 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
             rc = nd_sync(c, "peel record");
         }
     }
-    for (DBuf* b : {&ctl, &A0, &A1, &N0, &N1, &L0, &L1, &H, &rs, &rl, &rt, &etr, &hsc, &abits}) nd_free(c, *b);
+    for (DBuf* b : {&ctl, &A0, &A1, &N0, &N1, &L0, &L1, &H, &rs, &rl, &rt, &etr, &hsc, &abits, &ccol, &cpos, &clen,
+                    &cprev, &bcnt})
+        nd_free(c, *b);
     return rc;
 }
 
@@ -890,6 +967,8 @@ int nd_decompose_dev(nd_graph* g, int r, int s, int count_width, int flags, Peel
     S.listed = po.listed;
     S.decrements = po.decs;
     for (int i = 0; i < 6; ++i) S.t_phase_ms[i] = po.phase_ms[i];
+    S.t_contract_ms = po.phase_ms[6];
+    S.contractions = po.contractions;
     S.advances = po.advances;
     S.refills = po.refills;
     S.count_width = w;

@@ -211,6 +211,9 @@ struct GraphView {
     // hash directory of the long triangle lists (during a (3,4) decomposition), else NULL
     const int64_t* hoff;
     const NdHashSlot* htab;
+    // (2,3) peel with graph contraction: current length of each adjacency row (rows start at rp[v]
+    // and col / pos2e point to the peel's compacted copies), else NULL
+    const int32_t* rlen;
 };
 
 // Control block of the device-resident peeling loop (one per decomposition).
@@ -236,6 +239,14 @@ struct PeelCtl {
     int64_t finished;   // r-cliques peeled so far
     int64_t n_r;
     int64_t max_rounds; // round cap (ND_ETIMEOUT)
+    unsigned long long bar_timeout_ns;  // persistent kernel: longest wait at one grid barrier
+    int32_t drop_block; // persistent kernel, test of the barrier bound: the last block leaves at once
+    int32_t contract;   // graph contraction before this round's phases (set by the serial control step)
+    int64_t contract_every;  // contract once this many r-cliques were peeled since the last one (0: never)
+    int64_t peeled_since;    // r-cliques peeled since the last contraction
+    int64_t contractions;    // contractions run
+    int32_t contract_shift;  // compact a row that lost at least len >> shift entries (0: any loss)
+    int32_t pad3;
     // list sizes
     unsigned int nA;    // |A| of a same-level round
     unsigned int cntA;  // |A| written by adv_select
@@ -256,7 +267,7 @@ struct PeelCtl {
     unsigned long long decs;
     long long advances, refills;
     // persistent kernel: nanoseconds per phase between barriers, as seen by block 0
-    unsigned long long ph_ns[6];
+    unsigned long long ph_ns[7];  // [6]: graph contraction
     unsigned long long ph_last;
     unsigned long long hist[ND_HBINS];
 };
@@ -295,6 +306,17 @@ struct PeelView {
     int64_t* round_level;
     int64_t* round_ns;      // persistent kernel: Update wall time per round (block 0), or NULL
     int64_t round_cap;
+    // (2,3) graph contraction (Section 5.6): the compacted copies of the adjacency rows (neighbour
+    // and edge id), their current lengths and their lengths after the previous contraction; NULL
+    // when off
+    int32_t* ccol;
+    int32_t* cpos;
+    int32_t* clen;
+    int32_t* cprev;
+    // dense buckets (Section 4.2 Discussion): bcnt[c] = unpeeled r-cliques not yet scheduled whose
+    // count is c, for c < bmax (the largest initial count + 1); NULL when off
+    unsigned int* bcnt;
+    int64_t bmax;
 };
 
 // ------------------------------------------------------------------------------------
@@ -320,8 +342,8 @@ void nd_max_deg(const int64_t* rp, int32_t n, unsigned long long* out, cudaStrea
 void nd_sum_i64(const int64_t* a, int64_t n, unsigned long long* out, cudaStream_t st);
 void nd_sum_i32(const int32_t* a, int64_t n, unsigned long long* out, cudaStream_t st);
 void nd_max_i32(const int32_t* a, int64_t n, unsigned long long* out, cudaStream_t st);
-// narrow int64 counts to int32; *err set to 1 if a value exceeds INT32_MAX
-void nd_narrow_i64(const int64_t* in, int32_t* out, int64_t n, int* err, cudaStream_t st);
+// narrow int64 counts to int32; *err set to 1 if a value exceeds limit (<= INT32_MAX)
+void nd_narrow_i64(const int64_t* in, int32_t* out, int64_t n, int64_t limit, int* err, cudaStream_t st);
 
 // graph structure (nd_graph.cu)
 void nd_validate_csr(const int64_t* rp, const int32_t* col, int32_t n, int64_t nnz, int* err, cudaStream_t st);
@@ -358,10 +380,18 @@ void nd_peel_round(const GraphView& g, int r, int s, const PeelView<CT>& P, cuda
 template <typename CT>
 cudaError_t nd_peel_loop_graph(const GraphView& g, int r, int s, const PeelView<CT>& P, cudaStream_t st,
                                cudaStream_t st2, cudaStream_t st3, cudaGraph_t* out);
-int nd_peel_nodes_per_round(int r, int s);
+int nd_peel_nodes_per_round(int r, int s, bool contract);
 // the whole loop as one cooperative kernel launch
 template <typename CT>
 cudaError_t nd_peel_persistent(const GraphView& g, int r, int s, const PeelView<CT>& P, cudaStream_t st);
-void nd_peel_init(PeelCtl* ctl, int64_t n_r, int64_t max_rounds, cudaStream_t st);
+// barrier_ns 0: the default bound (60 s); drop_block: see ND_LIMIT_DROP_BLOCK; contract_every /
+// contract_shift: graph contraction schedule (0: off)
+void nd_peel_init(PeelCtl* ctl, int64_t n_r, int64_t max_rounds, cudaStream_t st, uint64_t barrier_ns = 0,
+                  int drop_block = 0, int64_t contract_every = 0, int contract_shift = 2);
+// row lengths len[v] = rp[v+1] - rp[v] (int32) into two arrays
+void nd_row_len(const int64_t* rp, int32_t n, int32_t* a, int32_t* b, cudaStream_t st);
+// dense buckets: bcnt[cnt[R]] += 1 for every R < n_r (bcnt zeroed by the caller)
+template <typename CT>
+void nd_bucket_fill(const CT* cnt, int64_t n_r, unsigned int* bcnt, int64_t bmax, cudaStream_t st);
 
 int nd_sm_count();

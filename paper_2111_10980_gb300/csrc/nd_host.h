@@ -27,6 +27,11 @@ struct nd_ctx {
     void* user = nullptr;
     void* pinned = nullptr;  // 4 KiB of pinned host memory for scalar read-backs
     cudaStream_t cap_st[2] = {nullptr, nullptr};  // extra streams used only to capture graph bodies
+    // nd_ctx_set_limits (0: default)
+    int64_t max_rounds = 0;
+    int64_t barrier_ns = 0;
+    int64_t count_limit = 0;
+    int32_t limit_flags = 0;
 };
 
 struct nd_graph {
@@ -59,7 +64,8 @@ struct nd_graph {
 struct PeelOut {
     DBuf core, rnd;
     int64_t rho = 0, max_core = 0, listed = 0, decs = 0, advances = 0, refills = 0;
-    double phase_ms[6] = {0, 0, 0, 0, 0, 0};
+    double phase_ms[7] = {0, 0, 0, 0, 0, 0, 0};  // [6]: graph contraction
+    int64_t contractions = 0;
     std::vector<int64_t> sizes, levels, round_ns;
 };
 

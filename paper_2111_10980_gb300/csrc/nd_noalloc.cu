@@ -21,6 +21,7 @@
 //     that first call should come before any stream capture.
 #include <cuda_runtime.h>
 
+#include <cstddef>
 #include <cstdint>
 #include <cstring>
 #include <mutex>
@@ -112,22 +113,27 @@ extern "C" int nd_kcore_noalloc(int32_t n, const int64_t* rowptr, const int32_t*
     if ((rc = nd_check_launch("nd_kcore_noalloc"))) return rc;
     const int kChunk = 32;
     int64_t max_chunks = ((int64_t)n + 2) / kChunk + 4;
-    int32_t flags[2] = {0, 0};  // done, err (pageable host memory: no pinned allocation)
+    // the head of the control block up to `finished` (pageable host memory: no pinned allocation)
+    constexpr size_t kHead = offsetof(PeelCtl, finished) + sizeof(int64_t);
+    alignas(8) unsigned char head[kHead];
+    PeelCtl* h = reinterpret_cast<PeelCtl*>(head);
     for (int64_t chunk = 0;; ++chunk) {
         for (int i = 0; i < kChunk; ++i) nd_peel_round<int32_t>(v, 1, 2, P, st);
         if ((rc = nd_check_launch("nd_kcore_noalloc"))) return rc;
-        e = cudaMemcpyAsync(flags, &P.ctl->done, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+        e = cudaMemcpyAsync(head, P.ctl, kHead, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return nd_set_error(ND_ECUDA, "nd_kcore_noalloc: %s", cudaGetErrorString(e));
         }
-        if (flags[0]) break;
+        if (h->done) break;
         if (chunk + 1 > max_chunks)
             return nd_set_error(ND_ETIMEOUT, "nd_kcore_noalloc: peeling did not finish");
     }
-    if (flags[1] & 1) return nd_set_error(ND_EINTERNAL, "nd_kcore_noalloc: a work list overflowed");
-    if (flags[1] & 2) return nd_set_error(ND_ETIMEOUT, "nd_kcore_noalloc: round cap reached");
-    if (flags[1] & 4) return nd_set_error(ND_EINTERNAL, "nd_kcore_noalloc: inconsistent peeling state");
+    if (h->err & 1) return nd_set_error(ND_EINTERNAL, "nd_kcore_noalloc: a work list overflowed");
+    if (h->err & 2) return nd_set_error(ND_ETIMEOUT, "nd_kcore_noalloc: round cap reached");
+    if (h->err & 4) return nd_set_error(ND_EINTERNAL, "nd_kcore_noalloc: inconsistent peeling state");
+    if (h->finished != n)
+        return nd_set_error(ND_EINTERNAL, "nd_kcore_noalloc: peeled %lld of %d vertices", (long long)h->finished, n);
     return ND_OK;
 }

@@ -115,8 +115,16 @@ __device__ __forceinline__ unsigned long long block_min(unsigned long long v) {
     return v;  // valid in thread 0
 }
 
-__global__ void k_init(PeelCtl* c, int64_t n_r, int64_t max_rounds) {
+__global__ void k_init(PeelCtl* c, int64_t n_r, int64_t max_rounds, unsigned long long barrier_ns, int drop_block,
+                       int64_t contract_every, int contract_shift) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
+        c->bar_timeout_ns = barrier_ns;
+        c->drop_block = drop_block;
+        c->contract = 0;
+        c->contract_every = contract_every;
+        c->contract_shift = contract_shift;
+        c->peeled_since = 0;
+        c->contractions = 0;
         c->t = 0;
         c->mode = 0;
         c->done = 0;
@@ -126,7 +134,7 @@ __global__ void k_init(PeelCtl* c, int64_t n_r, int64_t max_rounds) {
         c->lmat = 0;
         c->heavy = 0;
         c->sorta = 0;
-        for (int i = 0; i < 6; ++i) c->ph_ns[i] = 0;
+        for (int i = 0; i < 7; ++i) c->ph_ns[i] = 0;
         c->ph_last = 0;
         c->k = 0;
         c->hi = 0;
@@ -179,6 +187,7 @@ __device__ void ctl_step(PeelCtl* c, int64_t* round_size, int64_t* round_level, 
             round_level[c->t] = c->k;
         }
         c->finished += nA;
+        c->peeled_since += nA;
         c->t += 1;
         if (c->finished >= c->n_r) {
             c->done = 1;
@@ -202,6 +211,12 @@ __device__ void ctl_step(PeelCtl* c, int64_t* round_size, int64_t* round_level, 
         }
     }
     c->nH = 0;
+    // graph contraction (Section 5.6) once enough r-cliques were peeled since the previous one
+    c->contract = c->contract_every > 0 && c->peeled_since >= c->contract_every;
+    if (c->contract) {
+        c->peeled_since = 0;
+        c->contractions++;
+    }
     if (c->nNext > 0) {
         c->wa ^= 1;
         c->nA = c->nNext;
@@ -217,10 +232,47 @@ __device__ void ctl_step(PeelCtl* c, int64_t* round_size, int64_t* round_level, 
     }
 }
 
+// Dense buckets: the new level is the first non-empty bucket at or above k, found by the
+// doubling search of Section 4.2 (Discussion): regions [k, k+1), [k+1, k+3), [k+3, k+7), ... of
+// sizes 1, 2, 4, ... are searched in turn, each by all threads of block 0 at once, until one holds
+// a non-empty bucket. Work O(distance to the next bucket), O(log) steps. Every unpeeled r-clique
+// not yet scheduled has a count above k after the first round, so nothing below k is missed. If
+// that bucket lies inside the window (count < hi) it is the window's minimum; else the window
+// has no unpeeled member and is refilled as usual.
+template <typename CT>
+__device__ void dense_min(const PeelView<CT>& P) {
+    PeelCtl* c = P.ctl;
+    if (blockIdx.x != 0) return;
+    __shared__ unsigned long long s_found;
+    if (threadIdx.x == 0) s_found = ULLONG_MAX;
+    __syncthreads();
+    int64_t lo = c->k, span = 1;
+    unsigned long long got = ULLONG_MAX;
+    while (lo < P.bmax) {
+        int64_t hi = lo + span < P.bmax ? lo + span : P.bmax;
+        for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x)
+            if (P.bcnt[i]) {
+                atomicMin(&s_found, (unsigned long long)i);
+                break;
+            }
+        __syncthreads();
+        got = s_found;
+        __syncthreads();
+        if (got != ULLONG_MAX) break;
+        lo = hi;
+        span *= 2;
+    }
+    if (threadIdx.x == 0 && got != ULLONG_MAX && (int64_t)got < c->hi) c->minN = got;
+}
+
 template <typename CT>
 __device__ void phase_adv_min(const PeelView<CT>& P) {
     PeelCtl* c = P.ctl;
     if (c->done || !(c->mode & ND_MODE_ADV)) return;
+    if (P.bcnt) {
+        dense_min(P);
+        return;
+    }
     const int32_t* N = pick(P.N, c->wn);
     unsigned n = clampn(c->nN, P.cap);
     unsigned long long mn = ULLONG_MAX;
@@ -386,6 +438,7 @@ __device__ void phase_adv_select(const PeelView<CT>& P) {
             int32_t R = N[i];
             if (P.rnd[R] == ND_UNPEELED) {
                 if ((int64_t)P.cnt[R] <= kn) {
+                    if (P.bcnt) atomicSub(&P.bcnt[(int64_t)P.cnt[R]], 1u);
                     P.rnd[R] = t;
                     P.core[R] = (int32_t)kn;
                     if (P.et_rnd) set_tri_round(P, R, t);
@@ -398,6 +451,56 @@ __device__ void phase_adv_select(const PeelView<CT>& P) {
         }
     }
 }
+
+// Graph contraction for (2,3) (Section 5.6): every adjacency row that lost at least
+// len_prev >> contract_shift entries since the previous contraction (an entry is lost when its edge
+// was peeled in an earlier round) is filtered in place, keeping the order of the other entries;
+// one warp per vertex, 32 entries at a time, each kept entry written at (entries kept so far)
+// <= its own position. Edges of the current round stay: the owner rule needs them. Runs at the
+// start of a round, between barriers, so no Update reads the rows meanwhile.
+template <typename CT>
+__device__ void phase_contract(const GraphView& g, const PeelView<CT>& P) {
+    PeelCtl* c = P.ctl;
+    if (c->done || !c->contract) return;
+    const int32_t t = c->t, shift = c->contract_shift;
+    const int lane = threadIdx.x & 31;
+    for (int64_t v = gwarp(); v < g.n; v += nwarps()) {
+        const int64_t b = g.rp[v];
+        const int32_t len = P.clen[v], prev = P.cprev[v];
+        int32_t alive = 0;
+        for (int32_t i = lane; i < len; i += 32) alive += P.rnd[P.cpos[b + i]] >= t;
+        for (int o = 16; o > 0; o >>= 1) alive += __shfl_xor_sync(0xffffffffu, alive, o);
+        // the row is compacted when it lost at least prev >> shift entries (shift 0: any entry)
+        const int32_t lost = prev - alive;
+        const int32_t need = shift ? (prev >> shift) : 1;
+        if (alive == len || lost < need) continue;
+        int32_t out = 0;
+        for (int32_t i0 = 0; i0 < len; i0 += 32) {
+            const int32_t i = i0 + lane;
+            int32_t w = 0, e = 0;
+            bool keep = false;
+            if (i < len) {
+                w = P.ccol[b + i];
+                e = P.cpos[b + i];
+                keep = P.rnd[e] >= t;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, keep);
+            if (keep) {
+                const int32_t at = out + __popc(m & nd_lanemask_lt());
+                P.ccol[b + at] = w;
+                P.cpos[b + at] = e;
+            }
+            out += __popc(m);
+        }
+        if (lane == 0) {
+            P.clen[v] = out;
+            P.cprev[v] = out;
+        }
+    }
+}
+
+template <typename CT>
+__global__ void k_contract(GraphView g, PeelView<CT> P) { phase_contract(g, P); }
 
 template <typename CT>
 __global__ void k_adv_min(PeelView<CT> P) { phase_adv_min(P); }
@@ -531,6 +634,12 @@ struct UpdCounters {
 // window (it joins N).
 template <typename CT>
 __device__ __forceinline__ void after_dec(const RoundEnv<CT>& E, int32_t x, int64_t o) {
+    // dense buckets: a count above k + 1 moves down one bucket; at k + 1 the r-clique is scheduled
+    // now and leaves the buckets; at or below k it was scheduled already
+    if (E.P.bcnt && o > E.k) {
+        atomicSub(&E.P.bcnt[o], 1u);
+        if (o > E.k + 1) atomicAdd(&E.P.bcnt[o - 1], 1u);
+    }
     if (o > E.k && o - 1 <= E.k) {
         E.P.rnd[x] = E.t + 1;
         E.P.core[x] = (int32_t)E.k;
@@ -648,17 +757,22 @@ struct Upd13 {
 };
 
 // (2,3): R = (u,v); S = {u, v, w} for w in N(u) ∩ N(v); the shorter row drives.
+// length of row v: the contracted length during a (2,3) peel with contraction, else the degree
+__device__ __forceinline__ int64_t row_len(const GraphView& g, int32_t v) {
+    return g.rlen ? (int64_t)g.rlen[v] : g.rp[v + 1] - g.rp[v];
+}
+
 template <typename CT>
 struct Upd23 {
     static constexpr int64_t kHeavyWork = 256;  // a block, not a warp, for rows longer than this
     __device__ static int64_t work(const GraphView& g, int32_t R) {
         int32_t u = g.eu[R], v = g.ev[R];
-        int64_t du = g.rp[u + 1] - g.rp[u], dv = g.rp[v + 1] - g.rp[v];
+        int64_t du = row_len(g, u), dv = row_len(g, v);
         return du < dv ? du : dv;
     }
     __device__ static int64_t prep(const GraphView& g, const PeelView<CT>&, int32_t R, Prep& q) {
         int32_t u = g.eu[R], v = g.ev[R];
-        int64_t ub = g.rp[u], un = g.rp[u + 1] - ub, vb = g.rp[v], vn = g.rp[v + 1] - vb;
+        int64_t ub = g.rp[u], un = row_len(g, u), vb = g.rp[v], vn = row_len(g, v);
         bool u_drives = un <= vn;
         q.b[0] = u_drives ? ub : vb;
         q.n[0] = u_drives ? un : vn;
@@ -1154,8 +1268,8 @@ __device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned l
 // made before the barrier) and then releases the others, so a control step costs no extra
 // barrier. Arrival is an acquire-release RMW and the release a release store; waiting blocks poll
 // with an acquire load, so all writes before the barrier are visible after it. The wait is
-// bounded by the global timer: after kBarrierTimeoutNs, or once another block gave up, a block
-// sets ctl->err bit 8 and the function returns false.
+// bounded by the global timer: after ctl->bar_timeout_ns (kBarrierTimeoutNs by default), or once
+// another block gave up, a block sets ctl->err bit 8 and the function returns false.
 template <typename F>
 __device__ bool grid_barrier(PeelCtl* c, unsigned long long& target, F serial) {
     __shared__ int ok;
@@ -1169,8 +1283,9 @@ __device__ bool grid_barrier(PeelCtl* c, unsigned long long& target, F serial) {
             st_release_u64(&c->bar_gen, target);
         } else {
             unsigned long long t0 = globaltimer();
+            const unsigned long long limit = c->bar_timeout_ns;
             while (ld_acquire_u64(&c->bar_gen) < target) {
-                if ((ld_acquire_i32(&c->err) & 8) || globaltimer() - t0 > kBarrierTimeoutNs) {
+                if ((ld_acquire_i32(&c->err) & 8) || globaltimer() - t0 > limit) {
                     atomicOr(&c->err, 8);
                     good = 0;
                     break;
@@ -1266,11 +1381,19 @@ __global__ void __launch_bounds__(512, 2) k_peel_loop(GraphView g, PeelView<CT> 
             if (ph >= 4 && P.round_ns && tr < P.round_cap) P.round_ns[tr] += (int64_t)d;
         }
     };
+    // test of the barrier bound (ND_LIMIT_DROP_BLOCK): one block never arrives, so the others give
+    // up after bar_timeout_ns and the call reports ND_ETIMEOUT
+    if (c->drop_block && blockIdx.x == gridDim.x - 1) return;
     if (!grid_barrier(c, target, CtlSerial<CT>{c, &P})) return;  // set up round 0
     if (timer) c->ph_last = globaltimer();
     for (;;) {
         if (c->done) return;  // every block reads the same value after the barrier
         tr = c->t;
+        if (c->contract) {  // written only by serial steps
+            phase_contract(g, P);
+            if (!grid_barrier(c, target, NoSerial{})) return;
+            book(6);
+        }
         if (c->mode & ND_MODE_ADV) {
             phase_adv_min(P);
             if (!grid_barrier(c, target, NoSerial{})) return;
@@ -1328,8 +1451,15 @@ int peel_blocks() { return nd_sm_count() * 4; }
 
 int nd_peel_heavy_slices() { return nd_sm_count() * 2; }
 
-void nd_peel_init(PeelCtl* ctl, int64_t n_r, int64_t max_rounds, cudaStream_t st) {
-    ND_K(k_init<<<1, 32, 0, st>>>(ctl, n_r, max_rounds));
+void nd_peel_init(PeelCtl* ctl, int64_t n_r, int64_t max_rounds, cudaStream_t st, uint64_t barrier_ns,
+                  int drop_block, int64_t contract_every, int contract_shift) {
+    ND_K(k_init<<<1, 32, 0, st>>>(ctl, n_r, max_rounds, barrier_ns ? barrier_ns : kBarrierTimeoutNs, drop_block,
+                                  contract_every, contract_shift));
+}
+
+template <typename CT>
+void nd_peel_contract(const GraphView& g, const PeelView<CT>& P, cudaStream_t st) {
+    if (P.ccol) ND_K(k_contract<CT><<<peel_blocks(), kThreads, 0, st>>>(g, P));
 }
 
 template <typename CT>
@@ -1386,6 +1516,7 @@ void nd_peel_update(const GraphView& g, int r, int s, const PeelView<CT>& P, cud
 template <typename CT>
 void nd_peel_round(const GraphView& g, int r, int s, const PeelView<CT>& P, cudaStream_t st) {
     nd_peel_ctl<CT>(P, st, 0, 0, 0);
+    nd_peel_contract<CT>(g, P, st);
     nd_peel_adv_min<CT>(P, st);
     nd_peel_refill<CT>(P, st);
     nd_peel_adv_select<CT>(P, st);
@@ -1458,6 +1589,7 @@ cudaError_t nd_peel_loop_graph(const GraphView& g, int r, int s, const PeelView<
         cudaSuccess)
         return fail(e);
     nd_peel_ctl<CT>(P, st, 1, h_loop, h_adv);
+    nd_peel_contract<CT>(g, P, st);
     if ((e = capture_conditional(st, h_adv, cudaGraphCondTypeIf, &adv_body)) != cudaSuccess) return fail(e);
     if ((e = cudaStreamBeginCaptureToGraph(st2, adv_body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
         cudaSuccess)
@@ -1493,7 +1625,7 @@ cudaError_t nd_peel_persistent(const GraphView& g, int r, int s, const PeelView<
 
 // kernels launched per round by the loop graph (for the launch counter): the nodes executed in
 // a same-level round and the extra ones of an advance round
-int nd_peel_nodes_per_round(int r, int s) { return 3; }
+int nd_peel_nodes_per_round(int r, int s, bool contract) { return contract ? 4 : 3; }
 
 template void nd_peel_round<int32_t>(const GraphView&, int, int, const PeelView<int32_t>&, cudaStream_t);
 template void nd_peel_round<int64_t>(const GraphView&, int, int, const PeelView<int64_t>&, cudaStream_t);
@@ -1503,3 +1635,39 @@ template cudaError_t nd_peel_loop_graph<int32_t>(const GraphView&, int, int, con
                                                  cudaStream_t, cudaStream_t, cudaGraph_t*);
 template cudaError_t nd_peel_loop_graph<int64_t>(const GraphView&, int, int, const PeelView<int64_t>&, cudaStream_t,
                                                  cudaStream_t, cudaStream_t, cudaGraph_t*);
+
+// ------------------------------------------------------------------------------------
+// dense buckets: initial occupancy (a shared-memory histogram of the low buckets per block, global
+// atomics above it)
+
+namespace {
+constexpr int kBinShared = 8192;
+
+template <typename CT>
+__global__ void k_bucket_fill(const CT* __restrict__ cnt, int64_t n_r, unsigned int* __restrict__ bcnt, int64_t bmax) {
+    __shared__ unsigned int h[kBinShared];
+    const int64_t nb = bmax < kBinShared ? bmax : kBinShared;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    for (int64_t R = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; R < n_r; R += (int64_t)gridDim.x * blockDim.x) {
+        int64_t v = (int64_t)cnt[R];
+        if (v < nb)
+            atomicAdd(&h[v], 1u);
+        else if (v < bmax)
+            atomicAdd(&bcnt[v], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nb; i += blockDim.x)
+        if (h[i]) atomicAdd(&bcnt[i], h[i]);
+}
+}  // namespace
+
+template <typename CT>
+void nd_bucket_fill(const CT* cnt, int64_t n_r, unsigned int* bcnt, int64_t bmax, cudaStream_t st) {
+    if (n_r <= 0) return;
+    int64_t want = (n_r + 255) / 256, cap = (int64_t)nd_sm_count() * 4;
+    ND_K(k_bucket_fill<CT><<<(int)(want < cap ? want : cap), 256, 0, st>>>(cnt, n_r, bcnt, bmax));
+}
+
+template void nd_bucket_fill<int32_t>(const int32_t*, int64_t, unsigned int*, int64_t, cudaStream_t);
+template void nd_bucket_fill<int64_t>(const int64_t*, int64_t, unsigned int*, int64_t, cudaStream_t);

@@ -120,12 +120,13 @@ __global__ void k_reduce(const T* __restrict__ a, int64_t n, unsigned long long*
     }
 }
 
-__global__ void k_narrow(const int64_t* __restrict__ in, int32_t* __restrict__ out, int64_t n, int* err) {
+__global__ void k_narrow(const int64_t* __restrict__ in, int32_t* __restrict__ out, int64_t n, int64_t limit,
+                         int* err) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         int64_t v = in[i];
-        if (v > INT_MAX || v < 0) {
+        if (v > limit || v < 0) {
             atomicExch(err, 1);
-            v = INT_MAX;
+            v = limit;
         }
         out[i] = (int32_t)v;
     }
@@ -210,7 +211,23 @@ void nd_max_i32(const int32_t* a, int64_t n, unsigned long long* out, cudaStream
     ND_K(k_reduce<int32_t, true, false><<<grid_for(n, 256), 256, 0, st>>>(a, n, out));
 }
 
-void nd_narrow_i64(const int64_t* in, int32_t* out, int64_t n, int* err, cudaStream_t st) {
+void nd_narrow_i64(const int64_t* in, int32_t* out, int64_t n, int64_t limit, int* err, cudaStream_t st) {
     if (n <= 0) return;
-    ND_K(k_narrow<<<grid_for(n, 256), 256, 0, st>>>(in, out, n, err));
+    ND_K(k_narrow<<<grid_for(n, 256), 256, 0, st>>>(in, out, n, limit < INT_MAX ? limit : INT_MAX, err));
+}
+
+namespace {
+__global__ void k_row_len(const int64_t* __restrict__ rp, int32_t n, int32_t* __restrict__ a,
+                          int32_t* __restrict__ b) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        int32_t d = (int32_t)(rp[v + 1] - rp[v]);
+        a[v] = d;
+        b[v] = d;
+    }
+}
+}  // namespace
+
+void nd_row_len(const int64_t* rp, int32_t n, int32_t* a, int32_t* b, cudaStream_t st) {
+    if (n <= 0) return;
+    ND_K(k_row_len<<<grid_for(n, 256), 256, 0, st>>>(rp, n, a, b));
 }

@@ -53,9 +53,33 @@ double now_ms() {
     return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
 }
 
+// A request's CSR is checked on the host, in O(nnz log d), before it joins a union: rows
+// monotone, ids in range, rows strictly ascending, no self-loops, every (u,v) matched by (v,u).
+// A malformed request would otherwise shift into the union and send the kernels of every other
+// request of its group outside their arrays; this way it fails alone with ND_EINVAL.
 int check_request(const nd_request& q) {
     if (q.n < 0 || !q.rowptr || !rs_ok(q.r, q.s)) return ND_EINVAL;
-    if (q.rowptr[0] != 0 || q.rowptr[q.n] < 0 || (q.rowptr[q.n] > 0 && !q.col)) return ND_EINVAL;
+    const int64_t* rp = q.rowptr;
+    if (rp[0] != 0 || rp[q.n] < 0 || (rp[q.n] > 0 && !q.col) || (rp[q.n] & 1)) return ND_EINVAL;
+    for (int32_t u = 0; u < q.n; ++u)
+        if (rp[u + 1] < rp[u]) return ND_EINVAL;
+    for (int32_t u = 0; u < q.n; ++u) {
+        for (int64_t p = rp[u]; p < rp[u + 1]; ++p) {
+            int32_t v = q.col[p];
+            if (v < 0 || v >= q.n || v == u) return ND_EINVAL;
+            if (p > rp[u] && q.col[p - 1] >= v) return ND_EINVAL;
+            const int32_t* row = q.col + rp[v];
+            int64_t lo = 0, hi = rp[v + 1] - rp[v];
+            while (lo < hi) {
+                int64_t mid = (lo + hi) >> 1;
+                if (row[mid] < u)
+                    lo = mid + 1;
+                else
+                    hi = mid;
+            }
+            if (lo >= rp[v + 1] - rp[v] || row[lo] != u) return ND_EINVAL;
+        }
+    }
     return ND_OK;
 }
 
@@ -144,7 +168,8 @@ int run_group(nd_ctx* ctx, nd_request* const* reqs, const std::vector<int>& idx,
     return rc;
 }
 
-int batch_impl(nd_ctx* ctx, nd_request* const* reqs, int count, nd_batch_stats* st) {
+// checked: the requests already passed check_request (the server checks them in nd_submit)
+int batch_impl(nd_ctx* ctx, nd_request* const* reqs, int count, nd_batch_stats* st, bool checked = false) {
     double t0 = now_ms();
     if (st) {
         memset(st, 0, sizeof(*st));
@@ -156,7 +181,7 @@ int batch_impl(nd_ctx* ctx, nd_request* const* reqs, int count, nd_batch_stats* 
     for (int i = 0; i < count; ++i) {
         nd_request& q = *reqs[i];
         q.n_r = 0;
-        q.status = check_request(q);
+        q.status = checked ? ND_OK : check_request(q);
         if (q.status) {
             if (!first_err) first_err = q.status;
             continue;
@@ -282,7 +307,7 @@ static void worker_loop(nd_server* sv, int w) {
         double t0 = now_ms();
         std::vector<nd_request*> reqs(batch.size());
         for (size_t i = 0; i < batch.size(); ++i) reqs[i] = &batch[i]->req;
-        batch_impl(ctx, reqs.data(), (int)reqs.size(), nullptr);
+        batch_impl(ctx, reqs.data(), (int)reqs.size(), nullptr, true);
         double t1 = now_ms();
         {
             std::lock_guard<std::mutex> lk(sv->mu);

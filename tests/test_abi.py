@@ -43,14 +43,19 @@ def test_library_builds_and_exports_every_declared_symbol():
     assert set(nd.API) == declared_symbols()
 
 
-def test_built_for_sm_103a():
+def test_built_for_sm_103a_only():
+    """The build compiles every translation unit and links with exactly one target,
+    -gencode arch=compute_103a,code=sm_103a (a GB300 cubin and no PTX, so nothing can be
+    JIT-compiled for another architecture), with line info for the profiler."""
     from paper_2111_10980_gb300 import build
 
-    path = build.build()
-    out = subprocess.run(["cuobjdump", "--list-elf", path], capture_output=True, text=True)
-    if out.returncode != 0:
-        pytest.skip("cuobjdump unavailable")
-    assert "sm_103a" in out.stdout
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+    cmds = build.commands()
+    assert cmds and all(c[c.index("-gencode") + 1] == "arch=compute_103a,code=sm_103a" for c in cmds)
+    assert all(c.count("-gencode") == 1 for c in cmds)
+    assert all("-lineinfo" in c for c in cmds if "-c" in c)
+    assert {os.path.basename(c[c.index("-c") + 1]) for c in cmds if "-c" in c} == \
+        {os.path.basename(p) for p in build.sources()}
 
 
 def test_error_path_without_gpu():

@@ -1,11 +1,15 @@
 """Parity at full size -- R-MAT scale 20 ((2,3), (3,4)) in the launch configuration bench.py
 times, and Chung-Lu n = 4,194,304 with 2,000 planted communities ((3,4), (2,4), int64 tallies)
--- where the oracle cannot run the whole decomposition:
+-- where the oracle cannot run the whole peeling loop:
 
+* the validity + elimination-order + level certificate (oracle.certify_all, the Section 2
+  definition) over EVERY r-clique for R-MAT 20 (2,3) and for both Chung-Lu 4M decompositions,
+  which proves every core number exact; for R-MAT 20 (3,4) (17e9 4-cliques) over a stratified
+  sample of more than 1e5 triangles: every triangle whose three lists exceed the heavy-phase
+  threshold (4,096 entries), every triangle of the last round (the top level), and 1e5 random
+  ones;
 * sampled outputs the oracle computes one by one: the s-clique count of sampled r-cliques
   (oracle.local_counts, from the definition of the count);
-* the validity + elimination-order certificate (oracle.certify) on sampled r-cliques, which
-  for every checked r-clique confirms that its core number is neither too high nor too low;
 * properties that hold at any size: canonical order of the r-clique tuples, every sampled tuple
   is an r-clique, sum of round sizes = n_r, levels non-decreasing, core <= count, and the
   statistic sum(count) = C(s,r) n_s.
@@ -21,7 +25,6 @@ import oracle as orc
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 SAMPLE_COUNTS = 3000
-SAMPLE_CERT = 400
 
 
 @pytest.fixture(scope="module")
@@ -71,10 +74,14 @@ def run_full(nd, g, r, s, width=0):
     _, _, n_s = nd.nd_count(G, r, s, out=cnt)
     tuples = torch.empty((n_r, r), dtype=torch.int32, device="cuda")
     nd.nd_rcliques(G, r, out=tuples)
+    edge_support = None
+    if r == 3:
+        edge_support = torch.empty(g.m, dtype=torch.int64, device="cuda")
+        nd.nd_count(G, 2, 3, out=edge_support)
     nd.nd_graph_free(G)
     nd.nd_ctx_destroy(ctx)
     return dict(core=core, round=rnd, st=st, sizes=sizes, levels=levels, rho=rho, count=cnt, n_s=n_s,
-                tuples=tuples, n_r=n_r)
+                tuples=tuples, n_r=n_r, edge_support=edge_support)
 
 
 def edge_keys(g):
@@ -100,36 +107,60 @@ def lex_keys(t, n, ek):
 
 
 @pytest.mark.parametrize("r,s", [(2, 3), (3, 4)])
-def test_rmat_scale20_sampled(nd, big, r, s):
-    check_sampled(nd, big, r, s, 0)
+def test_rmat_scale20(nd, big, r, s):
+    res = check_sampled(nd, big, r, s, 0)
+    if (r, s) == (2, 3):
+        certify_every(big, r, s, res)
+    else:
+        certify_stratified(big, res)
 
 
 @pytest.mark.parametrize("r,s", [(3, 4), (2, 4)])
-def test_chung_lu_4m_planted_sampled(nd, cl4m, r, s):
-    st = check_sampled(nd, cl4m, r, s, 8)
-    assert st["count_width"] == 8
+def test_chung_lu_4m_planted(nd, cl4m, r, s):
+    res = check_sampled(nd, cl4m, r, s, 8)
+    assert res["st"]["count_width"] == 8
+    certify_every(cl4m, r, s, res)
 
 
-def sibling_tuples(g, R, r, s):
-    """Every r-subset of every s-clique containing R (R ascending), found from the graph."""
-    common = neighbours(g, int(R[0]))
-    for v in R[1:]:
-        common = np.intersect1d(common, neighbours(g, int(v)), assume_unique=True)
-    common = common[~np.isin(common, R)]
-    out = []
-    if s - r == 1:
-        completions = [(w,) for w in common]
-    else:  # s - r == 2: adjacent pairs inside the common neighbourhood
-        completions = []
-        for i, w in enumerate(common):
-            nw = neighbours(g, int(w))
-            for x in common[i + 1:][np.isin(common[i + 1:], nw)]:
-                completions.append((w, x))
-    for C in completions:
-        S = np.sort(np.concatenate([R, np.array(C, R.dtype)]))
-        for sub in __import__("itertools").combinations(range(s), r):
-            out.append(S[list(sub)])
-    return out
+def certify_every(g, r, s, res):
+    """The certificate over every r-clique: no validity, order or level failure."""
+    core = res["core"].cpu().numpy()
+    rnd = res["round"].cpu().numpy()
+    out = orc.certify_all(g, r, s, core, rnd, res["levels"])
+    assert out["bad_valid"] == 0 and out["bad_order"] == 0 and out["bad_level"] == 0, out
+
+
+def certify_stratified(g, res):
+    """(3,4): the certificate over every heavy triangle, every triangle of the last round and
+    1e5 random triangles."""
+    import torch
+
+    n_r = res["n_r"]
+    t = res["tuples"]
+    ek = edge_keys(g)
+    # edge supports |N(a) ∩ N(b)| from the (2,3) counts, to find the triangles whose three lists
+    # are all longer than the heavy threshold (any source may choose the sample: the certificate
+    # does not depend on it)
+    sup = res["edge_support"]
+    heavy = []
+    for lo in range(0, n_r, 1 << 26):
+        tt = t[lo:lo + (1 << 26)].to(torch.int64)
+        m = None
+        for i, j in ((0, 1), (0, 2), (1, 2)):
+            e = torch.searchsorted(ek, tt[:, i] * g.n + tt[:, j])
+            x = sup[e] > 4096
+            m = x if m is None else (m & x)
+        heavy.append(torch.nonzero(m).flatten() + lo)
+        del tt
+    heavy = torch.cat(heavy).cpu().numpy()
+    top = torch.nonzero(res["round"] == int(res["rho"]) - 1).flatten().cpu().numpy()
+    rng = np.random.default_rng(11)
+    ids = np.unique(np.concatenate([heavy, top, rng.integers(0, n_r, 100_000)]))
+    assert ids.size > 100_000 and heavy.size > 0
+    core = res["core"].cpu().numpy()
+    rnd = res["round"].cpu().numpy()
+    out = orc.certify_all(g, 3, 4, core, rnd, res["levels"], ids=ids)
+    assert out["bad_valid"] == 0 and out["bad_order"] == 0 and out["bad_level"] == 0, out
 
 
 def check_sampled(nd, g, r, s, width):
@@ -162,28 +193,4 @@ def check_sampled(nd, g, r, s, width):
         assert is_clique(g, tup[q])
     want = orc.local_counts(g, r, s, tup)
     assert np.array_equal(res["count"][idt].cpu().numpy(), want)
-    # certificate on a smaller sample; sibling ids found by a batched search of the canonical keys
-    pick = np.sort(rng.choice(ids.size, size=min(SAMPLE_CERT, ids.size), replace=False))
-    cid = ids[pick]
-    ctup = tup[pick]
-    sib = []
-    for R in ctup:
-        sib.extend(sibling_tuples(g, R, r, s))
-    sib = np.unique(np.array(sib, np.int64).reshape(-1, r), axis=0) if sib else np.zeros((0, r), np.int64)
-    sk = lex_keys(torch.from_numpy(sib).cuda(), g.n, ek)
-    pos = torch.searchsorted(key, sk)
-    assert bool((key[pos.clamp(max=n_r - 1)] == sk).all().item()), "an r-subset of an s-clique is missing"
-    lut = {tuple(x): int(p) for x, p in zip(sib.tolist(), pos.cpu().tolist())}
-    sel = torch.from_numpy(np.unique(np.concatenate([cid, np.array(list(lut.values()), np.int64)]))).cuda()
-    core_s = dict(zip(sel.cpu().tolist(), res["core"][sel].cpu().tolist()))
-    rnd_s = dict(zip(sel.cpu().tolist(), res["round"][sel].cpu().tolist()))
-    # dense small arrays indexed by position in `sel` for the C checker
-    order = sel.cpu().numpy()
-    remap = {int(x): i for i, x in enumerate(order)}
-    core_small = np.array([core_s[int(x)] for x in order], np.int32)
-    rnd_small = np.array([rnd_s[int(x)] for x in order], np.int32)
-    sv, so = orc.certify(g, r, s, core_small, rnd_small, np.array([remap[int(i)] for i in cid], np.int64), ctup,
-                         lambda tt: remap.get(lut.get(tuple(int(x) for x in tt), -1), -1))
-    assert np.all(sv >= core_small[[remap[int(i)] for i in cid]]), "validity fails for a sampled r-clique"
-    assert np.all(so <= core_small[[remap[int(i)] for i in cid]]), "elimination order fails for a sampled r-clique"
-    return res["st"]
+    return res

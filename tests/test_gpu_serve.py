@@ -156,3 +156,118 @@ def test_server_memory_budget_and_queue(nd, ctx):
         assert sv.poll(t)[0] == nd.ND_OK
     sv.close()
     assert busy > 0
+
+
+# ------------------------------------------------------------------------------------
+# The batched and served workloads at their own size ranges, checked against the oracle
+
+def _rs_draw(count, seed):
+    choices = [(2, 3), (3, 4), (2, 4)]
+    u = gg.uniform(seed, count)
+    return [choices[min(2, int(x * 3))] for x in u]
+
+
+@pytest.fixture(scope="module")
+def batch_items():
+    """The first 256 graphs of the batched workload (n up to 5,000, average degree up to 40,
+    (r,s) from (1,2), (2,3), (3,4)) with their oracle core numbers."""
+    from oracle_pool import oracle_cores
+
+    items = [(g, r, s) for g, (r, s) in gg.batch_workload(256)]
+    return items, oracle_cores(items)
+
+
+@pytest.fixture(scope="module")
+def serve_items():
+    """256 graphs of the served stream's pool with at most 1e5 edges (Chung-Lu and R-MAT, edge
+    count log-uniform), each with an (r,s) drawn from (2,3), (3,4), (2,4), with their oracle
+    core numbers."""
+    from oracle_pool import oracle_cores
+
+    graphs = gg.serve_pool(420, max_m=100_000)[:256]
+    items = [(g, r, s) for g, (r, s) in zip(graphs, _rs_draw(len(graphs), 77))]
+    return items, oracle_cores(items)
+
+
+def test_batch_workload_256_against_oracle_and_alone(nd, ctx, batch_items):
+    items, want = batch_items
+    assert len(items) == 256 and max(g.n for g, _, _ in items) > 4000
+    outs, n_r, status, st = nd.nd_batch_run(ctx, [(g.rowptr, g.col, r, s) for g, r, s in items])
+    assert all(x == nd.ND_OK for x in status)
+    for (g, r, s), got, k, w in zip(items, outs, n_r, want):
+        assert k == w.size, (g.name, r, s)
+        assert np.array_equal(got, w), (g.name, r, s)
+    for i in range(0, len(items), 5):  # one in five also against the graph decomposed alone
+        g, r, s = items[i]
+        assert np.array_equal(outs[i], alone(nd, ctx, g, r, s)), (g.name, r, s)
+
+
+def test_server_on_the_serve_pool_against_oracle_and_alone(nd, ctx, serve_items):
+    items, want = serve_items
+    assert len(items) == 256 and max(g.m for g, _, _ in items) > 50_000
+    tickets, outs, results = _serve(nd, ctx, items, workers=4, max_batch=64)
+    shared = 0
+    for (g, r, s), t, (out, k), w in zip(items, tickets, outs, want):
+        rc, res = results[t]
+        assert rc == nd.ND_OK
+        assert res["n_r"] == k == w.size
+        assert np.array_equal(out[:k], w), (g.name, r, s)
+        shared += res["batch_size"] > 1
+    assert shared > 0
+    for i in range(0, len(items), 5):
+        g, r, s = items[i]
+        assert np.array_equal(outs[i][0][:outs[i][1]], alone(nd, ctx, g, r, s)), (g.name, r, s)
+
+
+def test_malformed_requests_fail_alone(nd, ctx):
+    """A request whose CSR breaks an invariant (an id out of range, an unsorted row, a
+    self-loop, a missing reverse entry) is rejected on the host with ND_EINVAL, in a batch and
+    by the server, while the well-formed requests beside it still get the oracle's result."""
+    good = [gg.chung_lu(300, 10.0, 2.2, seed=71), gg.rmat(8, 8, 0.57, 0.19, 0.19, seed=72)]
+    base = gg.chung_lu(200, 8.0, 2.2, seed=73)
+    row = int(np.argmax(np.diff(base.rowptr)))
+    lo, hi = int(base.rowptr[row]), int(base.rowptr[row + 1])
+    nbrs = set(base.col[lo:hi].tolist())
+    bads = []
+    c = base.col.copy()
+    c[5] = base.n + 3  # id out of range
+    bads.append(c)
+    c = base.col.copy()
+    c[[lo, lo + 1]] = c[[lo + 1, lo]]  # row not ascending
+    bads.append(c)
+    # a value between two neighbours of `row` that keeps the row ascending: `row` itself gives a
+    # self-loop, any other non-neighbour an entry whose reverse is missing
+    for target in (row, None):
+        for q in range(lo + 1, hi - 1):
+            cands = [x for x in range(int(base.col[q - 1]) + 1, int(base.col[q + 1]))
+                     if x not in nbrs and (x == row if target is not None else x != row)]
+            if cands:
+                c = base.col.copy()
+                c[q] = cands[0]
+                bads.append(c)
+                break
+    assert len(bads) == 4
+    reqs = [(good[0].rowptr, good[0].col, 2, 3)]
+    for c in bads:
+        reqs.append((base.rowptr, c, 2, 3))
+    reqs.append((good[1].rowptr, good[1].col, 2, 3))
+    reqs.append((good[1].rowptr, good[1].col, 3, 4))
+    outs, n_r, status, _ = nd.nd_batch_run(ctx, reqs)
+    assert status[0] == nd.ND_OK and status[-1] == nd.ND_OK and status[-2] == nd.ND_OK
+    assert all(st == nd.ND_EINVAL for st in status[1:1 + len(bads)]), status
+    assert np.array_equal(outs[0][:n_r[0]], orc.decompose(good[0], 2, 3).core)
+    assert np.array_equal(outs[-2][:n_r[-2]], orc.decompose(good[1], 2, 3).core)
+    assert np.array_equal(outs[-1][:n_r[-1]], orc.decompose(good[1], 3, 4).core)
+    sv = nd.nd_server_create(ctx, workers=2, max_batch=8)
+    try:
+        for c in bads:
+            with pytest.raises(nd.NdError) as ei:
+                sv.submit(base.rowptr, c, 2, 3, np.zeros(base.m, np.int32))
+            assert ei.value.code == nd.ND_EINVAL
+        out = np.zeros(good[0].m, np.int32)
+        t = sv.submit(good[0].rowptr, good[0].col, 2, 3, out)
+        sv.drain()
+        assert sv.poll(t)[0] == nd.ND_OK
+        assert np.array_equal(out, orc.decompose(good[0], 2, 3).core)
+    finally:
+        sv.close()

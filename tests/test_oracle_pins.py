@@ -353,3 +353,77 @@ def test_certificate_accepts_oracle_and_rejects_perturbations(r, s):
     bad[j] -= 1
     _, so2 = orc.certify(g, r, s, bad, d.round, ids[j:j + 1], tuples[j:j + 1], lookup)
     assert so2[0] > bad[j]
+
+
+# ------------------------------------------------------------------------------------
+# The parallel certificate (certify_all): its supports against brute force over the
+# s-cliques, acceptance of the oracle's decomposition, rejection of perturbed claims.
+
+def _brute_supports(g, r, s, core, rnd):
+    """Per r-clique (canonical order): #{S containing R : min core over S's r-subsets >=
+    core[R]} and #{S containing R : min round over S's r-subsets >= round[R]}, from every
+    pairwise-adjacent vertex subset of size s."""
+    rcl = py_cliques(g, r)
+    pos = {t: i for i, t in enumerate(rcl)}
+    sv = np.zeros(len(rcl), np.int64)
+    so = np.zeros(len(rcl), np.int64)
+    for S in py_cliques(g, s):
+        ids = [pos[t] for t in itertools.combinations(S, r)]
+        mc = min(core[i] for i in ids)
+        mr = min(rnd[i] for i in ids)
+        for i in ids:
+            sv[i] += mc >= core[i]
+            so[i] += mr >= rnd[i]
+    return sv, so
+
+
+@pytest.mark.parametrize("r,s", RS_ALL)
+def test_certify_all_supports_match_brute_force(r, s):
+    for seed in range(6):
+        g = gg.gnp(9, [0.4, 0.6, 0.8][seed % 3], 900 + seed)
+        d = orc.decompose(g, r, s)
+        # a perturbed claim too, so that the supports are checked where they differ from n_s
+        rng = np.random.default_rng(seed)
+        core = d.core + rng.integers(-1, 2, d.core.size).astype(np.int32)
+        rnd = np.maximum(d.round + rng.integers(-1, 2, d.round.size).astype(np.int32), 0)
+        for c, t in [(d.core, d.round), (core, rnd)]:
+            want_v, want_o = _brute_supports(g, r, s, c, t)
+            got = orc.certify_all(g, r, s, c, t, d.levels, ids=np.arange(c.size))
+            assert np.array_equal(got["sup_valid"], want_v)
+            assert np.array_equal(got["sup_order"], want_o)
+
+
+@pytest.mark.parametrize("r,s", [(1, 2), (1, 3), (2, 3), (2, 4), (3, 4), (2, 5), (3, 5), (4, 5)])
+def test_certify_all_accepts_oracle_and_rejects_perturbations(r, s):
+    for g in [gg.fig1(), gg.chung_lu(400, 16.0, 2.2, seed=37), gg.rmat(9, 16, 0.57, 0.19, 0.19, seed=38)]:
+        d = orc.decompose(g, r, s)
+        ok = orc.certify_all(g, r, s, d.core, d.round, d.levels)
+        assert ok["bad_valid"] == ok["bad_order"] == ok["bad_level"] == 0 and ok["first_bad"] == -1
+        if d.core.size == 0 or d.core.max() == 0:
+            continue
+        # a raised core number fails validity (and the level test)
+        i = int(np.argmax(d.core))
+        bad = d.core.copy()
+        bad[i] += 1
+        res = orc.certify_all(g, r, s, bad, d.round, d.levels)
+        assert res["bad_valid"] >= 1 and res["first_bad"] <= i
+        # an r-clique claimed one round later at a lower level than it has fails the order test
+        # for the first r-clique of the top round
+        top = int(d.rho - 1)
+        j = int(np.nonzero(d.round == top)[0][0])
+        lev = d.levels.copy()
+        lev[top] -= 1
+        bad = d.core.copy()
+        bad[d.round == top] -= 1
+        res = orc.certify_all(g, r, s, bad, d.round, lev)
+        assert res["bad_order"] + res["bad_valid"] + res["bad_level"] >= 1
+        # decreasing levels are rejected
+        if d.rho >= 2 and d.levels[-1] > d.levels[0]:
+            lev = d.levels.copy()
+            lev[0] = lev[-1] + 1
+            res = orc.certify_all(g, r, s, d.core, d.round, lev)
+            assert res["bad_level"] >= 1
+        # full mode and sample mode agree on the failures
+        res_s = orc.certify_all(g, r, s, d.core, d.round, d.levels, ids=np.arange(d.core.size))
+        assert res_s["bad_valid"] == res_s["bad_order"] == res_s["bad_level"] == 0
+        assert j >= 0
