@@ -84,6 +84,10 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--peel-mode", choices=["default", "persistent", "loop_graph", "plain"], default="default",
                     help="how the peeling rounds are launched (default: the library's choice)")
+    ap.add_argument("--contract", choices=["default", "off", "always"], default="default",
+                    help="(2,3) graph contraction: the paper's schedule (default), off, or before every round")
+    ap.add_argument("--dense-buckets", action="store_true", help="level advances by the dense-bucket search")
+    ap.add_argument("--rs", default=None, help="only these (r,s) of the workload, e.g. 2,3 or 2,3:3,4")
     ap.add_argument("--scale", type=int, default=None,
                     help="R-MAT workload only: use scale S instead of 20 (profiling a smaller case)")
     return ap.parse_args()
@@ -262,6 +266,8 @@ def main():
         wl["gen"] = lambda: gg.rmat(sc, 16, 0.57, 0.19, 0.19, seed=2)
         wl["desc"] = wl["desc"].replace("scale 20", f"scale {sc}")
         workload_name = f"rmat{sc}"
+    if args.rs:
+        wl["rs"] = [tuple(int(x) for x in p.split(",")) for p in args.rs.split(":")]
     wl["name"] = workload_name
     g = wl["gen"]()
     stream = torch.cuda.Stream(device=local)
@@ -275,6 +281,9 @@ def main():
     outs = {}
     pflags = {"default": 0, "persistent": nd.ND_PEEL_PERSISTENT, "loop_graph": nd.ND_PEEL_LOOP_GRAPH,
               "plain": nd.ND_NO_GRAPH}[args.peel_mode]
+    pflags |= {"default": 0, "off": nd.ND_CONTRACT_OFF, "always": nd.ND_CONTRACT_ALWAYS}[args.contract]
+    if args.dense_buckets:
+        pflags |= nd.ND_DENSE_BUCKETS
 
     def step():
         nd.nd_graph_reset(G)  # every step rebuilds orientation and indexes
@@ -333,13 +342,15 @@ def main():
             "config": {"workload": workload_name, "desc": wl["desc"], "n": g.n, "m": g.m,
                        "rs": [f"({r},{s})" for r, s in wl["rs"]], "parallelism": f"replicas x{world}",
                        "l2": "flushed between steps (256 MiB write, outside the step events)",
-                       "peel_mode": args.peel_mode},
+                       "peel_mode": args.peel_mode, "contract": args.contract,
+                       "dense_buckets": bool(args.dense_buckets)},
             "r_cliques_peeled_per_s": peeled_per_s,
             "wall_s_timed": wall,
             "per_rs": {f"({r},{s})": dict(
                 {k: stats[(r, s)][k] for k in
                  ("n_r", "n_s", "rho", "max_core", "listed", "decrements", "advances", "refills", "count_width",
-                  "t_orient_ms", "t_index_ms", "t_count_ms", "t_peel_ms", "t_total_ms", "t_phase_ms")},
+                  "t_orient_ms", "t_index_ms", "t_count_ms", "t_peel_ms", "t_total_ms", "t_phase_ms",
+                  "t_contract_ms", "contractions")},
                 # the count phase alone (s-cliques counted per second) and the peel alone
                 n_s_per_s_count=stats[(r, s)]["n_s"] / max(stats[(r, s)]["t_count_ms"], 1e-9) * 1e3,
                 n_r_per_s_peel=stats[(r, s)]["n_r"] / max(stats[(r, s)]["t_peel_ms"], 1e-9) * 1e3)

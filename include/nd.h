@@ -26,7 +26,9 @@
  *   - Canonical r-clique order (the id space of all per-r-clique outputs): r-cliques sorted
  *     lexicographically by their ascending tuple of vertex ids. r = 1: vertex id; r = 2:
  *     edges (u < v) in CSR order; r = 3: triangles (a < b < c) by (a, b, c).
- *   - Supported (r, s): (1,2), (1,3), (2,3), (2,4), (3,4). Others return ND_EINVAL.
+ *   - Supported (r, s): (1,2), (1,3), (2,3), (2,4), (3,4) with kernels of their own, and (1,4),
+ *     (2,5), (3,5), (3,6) through the generic listing of the (s-r)-cliques of each r-clique's
+ *     common neighbourhood. Others return ND_EINVAL.
  *   - All work is issued on the context's stream; synchronous calls synchronise that stream
  *     before returning.
  */

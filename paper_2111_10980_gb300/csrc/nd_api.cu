@@ -487,7 +487,7 @@ static int ensure_tri(nd_graph* g) {
 }
 
 static bool rs_supported(int r, int s) {
-    return (r == 1 && (s == 2 || s == 3)) || (r == 2 && (s == 3 || s == 4)) || (r == 3 && s == 4);
+    return (r == 1 && s >= 2 && s <= 4) || (r == 2 && s >= 3 && s <= 5) || (r == 3 && s >= 4 && s <= 6);
 }
 
 static int64_t binom64(int64_t a, int b) {
@@ -691,7 +691,7 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
     if ((rc = nd_alloc(c, ctl, sizeof(PeelCtl))) || (rc = nd_alloc(c, A0, 4 * cap)) || (rc = nd_alloc(c, A1, 4 * cap)) ||
         (rc = nd_alloc(c, N0, 4 * cap)) || (rc = nd_alloc(c, N1, 4 * cap)) || (rc = nd_alloc(c, L0, 4 * cap)) ||
         (rc = nd_alloc(c, L1, 4 * cap)) || (rc = nd_alloc(c, H, 4 * hcap)) || (rc = nd_alloc(c, rs, 8 * rcap)) ||
-        (rc = nd_alloc(c, rl, 8 * rcap)) || (rc = nd_alloc(c, rt, 8 * rcap)) || (r == 3 && (rc = nd_alloc(c, etr, 4 * std::max<int64_t>(3 * g->n3, 1)))) ||
+        (rc = nd_alloc(c, rl, 8 * rcap)) || (rc = nd_alloc(c, rt, 8 * rcap)) || (r == 3 && s == 4 && (rc = nd_alloc(c, etr, 4 * std::max<int64_t>(3 * g->n3, 1)))) ||
         (staged && (rc = nd_alloc(c, hsc, 4 * 5 * (hstage + 1) * hslices))) ||
         (rc = nd_alloc(c, abits, r == 3 ? 4 * ((cap + 31) / 32) : 4)) ||
         (contract && ((rc = nd_alloc(c, ccol, 4 * std::max<int64_t>(g->nnz, 1))) ||
@@ -740,7 +740,7 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
     P.hoff = nullptr;
     P.htab = nullptr;
     P.hpos = nullptr;
-    if (r == 3) {
+    if (r == 3 && s == 4) {
         // the hash directory, when the decomposition built one (nd_decompose_dev, (3,4))
         P.hoff = (const int64_t*)g->hoff.p;
         P.htab = (NdHashSlot*)g->htab.p;
@@ -878,6 +878,7 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
             else if (h.err & 1) rc = nd_set_error(ND_EINTERNAL, "peel: a work list overflowed");
             else if (h.err & 2) rc = nd_set_error(ND_ETIMEOUT, "peel: round cap reached");
             else if (h.err & 4) rc = nd_set_error(ND_EINTERNAL, "peel: empty round (inconsistent state)");
+            else if (h.err & 16) rc = nd_set_error(ND_EINTERNAL, "peel: an r-subset of a listed s-clique is not in the index");
             else if (h.finished != n_r) rc = nd_set_error(ND_EINTERNAL, "peel: finished %lld of %lld",
                                                           (long long)h.finished, (long long)n_r);
             po.rho = h.t;

@@ -12,6 +12,7 @@
 //     to each of their C(s,r) r-subsets (Count-Func), with one aggregated atomic for the
 //     r-subsets shared by a whole level.
 #include "nd_common.cuh"
+#include "nd_gen.cuh"
 
 namespace {
 
@@ -172,6 +173,25 @@ __global__ void k_count24(GraphView g, CT* __restrict__ cnt) {
     }
 }
 
+// Any other supported (r,s) ((1,4), (2,5), (3,5), (3,6)): one warp per r-clique R counts the
+// s-cliques containing it, listing the (s-r)-cliques of R's common neighbourhood from the entries
+// of its driving list (nd_gen.cuh); written once, no atomics.
+template <typename CT, int R_, int S_>
+__global__ void k_count_gen(GraphView g, CT* __restrict__ cnt, int64_t n_r) {
+    int lane = threadIdx.x & 31;
+    for (int64_t id = gwarp(); id < n_r; id += nwarps()) {
+        int32_t v[3];
+        gen_verts<R_>(g, id, v);
+        const int32_t* list = nullptr;
+        int64_t len = 0;
+        gen_drive<R_>(g, id, v, list, len);
+        unsigned long long c = 0;
+        for (int64_t j = lane; j < len; j += 32) gen_cand<R_, S_>(g, v, list[j], [&](const int32_t*) { ++c; });
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+        if (lane == 0) cnt[id] = (CT)c;
+    }
+}
+
 template <typename CT>
 __global__ void k_zero(CT* p, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -196,6 +216,14 @@ void nd_count_launch(const GraphView& g, int r, int s, CT* cnt, int64_t n_r, cud
     } else if (r == 2 && s == 4) {
         ND_K(k_zero<CT><<<blk, kThreads, 0, st>>>(cnt, n_r));
         ND_K(k_count24<CT><<<blocks_for_warps(g.n), kThreads, 0, st>>>(g, cnt));
+    } else if (r == 1 && s == 4) {
+        ND_K(k_count_gen<CT, 1, 4><<<blk, kThreads, 0, st>>>(g, cnt, n_r));
+    } else if (r == 2 && s == 5) {
+        ND_K(k_count_gen<CT, 2, 5><<<blk, kThreads, 0, st>>>(g, cnt, n_r));
+    } else if (r == 3 && s == 5) {
+        ND_K(k_count_gen<CT, 3, 5><<<blk, kThreads, 0, st>>>(g, cnt, n_r));
+    } else if (r == 3 && s == 6) {
+        ND_K(k_count_gen<CT, 3, 6><<<blk, kThreads, 0, st>>>(g, cnt, n_r));
     }
 }
 

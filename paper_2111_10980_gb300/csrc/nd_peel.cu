@@ -32,6 +32,7 @@
 //     has each of the a members of A subtract 1/a; the owner rule gives the same total (1 per
 //     live S and surviving member) with integer atomics and without double counting.
 #include "nd_common.cuh"
+#include "nd_gen.cuh"
 
 #include <climits>
 #include <cstring>
@@ -702,6 +703,8 @@ struct Prep {
     int64_t b[3];
     int64_t n[3];
     int64_t h[3];  // (3,4): hash-table offset of the list, -1 when it is searched by bisection
+    int32_t v[3];  // generic (r,s): the vertices of R
+    const int32_t* lp;  // generic (r,s): the driving list
 };
 
 // The light Update phase gives each warp one R at a time: its lanes share the R's lists and read
@@ -1107,6 +1110,35 @@ struct Upd34 {
     }
 };
 
+// Any other (r,s) with r <= 3 and s - r <= 3 ((1,4), (2,5), (3,5), (3,6)): the candidates are
+// the entries of R's driving list; each lists the (s-r)-cliques of R's common neighbourhood that
+// start at it (nd_gen.cuh), looks up the ids of the other r-subsets of every S = R + C and applies
+// Update-Func. A lookup that fails means an inconsistent index (ctl->err bit 16).
+template <typename CT, int R_, int S_>
+struct UpdGen {
+    static constexpr int M = gen_binom(S_, R_) - 1;
+    __device__ static int64_t prep(const GraphView& g, const PeelView<CT>&, int32_t R, Prep& q) {
+        gen_verts<R_>(g, R, q.v);
+        int64_t len = 0;
+        gen_drive<R_>(g, R, q.v, q.lp, len);
+        q.n[0] = len;
+        return len;
+    }
+    template <typename Q>
+    __device__ static void cand(const GraphView& g, const RoundEnv<CT>& E, int32_t R, const Q& q, int64_t j,
+                                UpdCounters& k) {
+        gen_cand<R_, S_>(g, q.v, q.lp[j], [&](const int32_t* C) {
+            int32_t Sv[S_], o[M];
+            gen_merge<R_, S_>(q.v, C, Sv);
+            if (!gen_others<R_, S_>(g, q.v, Sv, o)) {
+                atomicOr(&E.P.ctl->err, 16);
+                return;
+            }
+            update_func<CT, M>(E, R, o, k);
+        });
+    }
+};
+
 template <typename U, typename = void>
 struct has_pair {
     static constexpr bool value = false;
@@ -1509,6 +1541,18 @@ void nd_peel_update(const GraphView& g, int r, int s, const PeelView<CT>& P, cud
     } else if (r == 3 && s == 4) {
         ND_K(k_update<CT, Upd34<CT>><<<nb, kThreads, 0, st>>>(g, P));
         ND_K(k_update_heavy<CT, Upd34<CT>><<<nb, kThreads, 0, st>>>(g, P));
+    } else if (r == 1 && s == 4) {
+        ND_K(k_update<CT, UpdGen<CT, 1, 4>><<<nb, kThreads, 0, st>>>(g, P));
+        ND_K(k_update_heavy<CT, UpdGen<CT, 1, 4>><<<nb, kThreads, 0, st>>>(g, P));
+    } else if (r == 2 && s == 5) {
+        ND_K(k_update<CT, UpdGen<CT, 2, 5>><<<nb, kThreads, 0, st>>>(g, P));
+        ND_K(k_update_heavy<CT, UpdGen<CT, 2, 5>><<<nb, kThreads, 0, st>>>(g, P));
+    } else if (r == 3 && s == 5) {
+        ND_K(k_update<CT, UpdGen<CT, 3, 5>><<<nb, kThreads, 0, st>>>(g, P));
+        ND_K(k_update_heavy<CT, UpdGen<CT, 3, 5>><<<nb, kThreads, 0, st>>>(g, P));
+    } else if (r == 3 && s == 6) {
+        ND_K(k_update<CT, UpdGen<CT, 3, 6>><<<nb, kThreads, 0, st>>>(g, P));
+        ND_K(k_update_heavy<CT, UpdGen<CT, 3, 6>><<<nb, kThreads, 0, st>>>(g, P));
     }
 }
 
@@ -1620,6 +1664,10 @@ cudaError_t nd_peel_persistent(const GraphView& g, int r, int s, const PeelView<
     if (r == 2 && s == 3) return launch_peel_loop<CT, Upd23<CT>, false>(g, P, st);
     if (r == 2 && s == 4) return launch_peel_loop<CT, Upd24<CT>, false>(g, P, st);
     if (r == 3 && s == 4) return launch_peel_loop<CT, Upd34<CT>, true>(g, P, st);
+    if (r == 1 && s == 4) return launch_peel_loop<CT, UpdGen<CT, 1, 4>, false>(g, P, st);
+    if (r == 2 && s == 5) return launch_peel_loop<CT, UpdGen<CT, 2, 5>, false>(g, P, st);
+    if (r == 3 && s == 5) return launch_peel_loop<CT, UpdGen<CT, 3, 5>, false>(g, P, st);
+    if (r == 3 && s == 6) return launch_peel_loop<CT, UpdGen<CT, 3, 6>, false>(g, P, st);
     return cudaErrorInvalidValue;
 }
 

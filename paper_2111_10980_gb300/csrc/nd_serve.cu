@@ -34,7 +34,7 @@
 namespace {
 
 bool rs_ok(int r, int s) {
-    return (r == 1 && (s == 2 || s == 3)) || (r == 2 && (s == 3 || s == 4)) || (r == 3 && s == 4);
+    return (r == 1 && s >= 2 && s <= 4) || (r == 2 && s >= 3 && s <= 5) || (r == 3 && s >= 4 && s <= 6);
 }
 
 __global__ void k_gather_offsets(const int64_t* __restrict__ ebase, const int64_t* __restrict__ tbase,
