@@ -256,6 +256,8 @@ struct PeelCtl {
     unsigned int nL;    // |L|
     unsigned int nL2;   // |L'| being written by refill
     unsigned int nH;    // r-cliques of this round's A deferred to the heavy Update kernel
+    unsigned int upd_next;  // next unassigned position of A in this round's Update (dynamic chunks)
+    unsigned int upd_pad;
     unsigned long long minN;  // min count over unpeeled members of N (adv_min)
     unsigned long long gmin;  // min count over unpeeled r-cliques (refill)
     // grid barrier of the persistent peel kernel: arrivals since the launch, and the arrival

@@ -143,6 +143,7 @@ __global__ void k_init(PeelCtl* c, int64_t n_r, int64_t max_rounds, unsigned lon
         c->n_r = n_r;
         c->max_rounds = max_rounds;
         c->nA = c->cntA = c->nNext = c->nN = c->nN2 = c->nL = c->nL2 = c->nH = 0;
+        c->upd_next = 0;
         c->minN = c->gmin = ULLONG_MAX;
         c->listed = 0;
         c->decs = 0;
@@ -212,6 +213,7 @@ __device__ void ctl_step(PeelCtl* c, int64_t* round_size, int64_t* round_level, 
         }
     }
     c->nH = 0;
+    c->upd_next = 0;
     // graph contraction (Section 5.6) once enough r-cliques were peeled since the previous one
     c->contract = c->contract_every > 0 && c->peeled_since >= c->contract_every;
     if (c->contract) {
@@ -1167,6 +1169,22 @@ struct heavy_work<U, decltype((void)U::kHeavyWork)> {
     static constexpr int64_t value = U::kHeavyWork;
 };
 
+// Update hands out A to warps in chunks taken from a counter that the round's control step resets:
+// a warp that finishes early takes more, so the round ends when the work ends rather than when the
+// unluckiest warp of a static assignment does. A chunk holds about nA / (16 warps) r-cliques (at
+// least 1), so a round costs about 16 counter updates per warp however large A is.
+__device__ __forceinline__ unsigned update_chunk(unsigned nA) {
+    unsigned long long w = (unsigned long long)nwarps() * 16ull;
+    unsigned long long c = nA / w;
+    return c ? (unsigned)c : 1u;
+}
+
+__device__ __forceinline__ unsigned take_chunk(PeelCtl* c, unsigned chunk) {
+    unsigned i0 = 0;
+    if ((threadIdx.x & 31) == 0) i0 = atomicAdd(&c->upd_next, chunk);
+    return __shfl_sync(0xffffffffu, i0, 0);
+}
+
 template <typename CT, typename U>
 __device__ void phase_update(const GraphView& g, const PeelView<CT>& P) {
     if (P.ctl->done) return;
@@ -1178,7 +1196,9 @@ __device__ void phase_update(const GraphView& g, const PeelView<CT>& P) {
         // one warp per r-clique, I staged in the warp's shared memory
         __shared__ int32_t s_w[kMaxWarpsPerBlock][kI24], s_x[kMaxWarpsPerBlock][kI24],
             s_y[kMaxWarpsPerBlock][kI24], s_b[kMaxWarpsPerBlock][kI24], s_p[kMaxWarpsPerBlock][kI24 + 1];
-        for (int64_t i = gwarp(); i < E.nA; i += nwarps()) {
+        const unsigned chunk = update_chunk(E.nA);
+        for (unsigned i0 = take_chunk(P.ctl, chunk); i0 < E.nA; i0 = take_chunk(P.ctl, chunk))
+        for (unsigned i = i0; i < i0 + chunk && i < E.nA; ++i) {
             int32_t R = E.A[i];
             if (lane == 0) unmark_a(P, R);
             if (U::work(g, R) > heavy_work<U>::value) {
@@ -1201,7 +1221,9 @@ __device__ void phase_update(const GraphView& g, const PeelView<CT>& P) {
         }
     } else {
         // one warp per r-clique: its lanes read the driving list coalesced
-        for (int64_t i = gwarp(); i < E.nA; i += nwarps()) {
+        const unsigned chunk = update_chunk(E.nA);
+        for (unsigned i0 = take_chunk(P.ctl, chunk); i0 < E.nA; i0 = take_chunk(P.ctl, chunk))
+        for (unsigned i = i0; i < i0 + chunk && i < E.nA; ++i) {
             int32_t R = E.A[i];
             if (lane == 0) unmark_a(P, R);
             Prep q;
@@ -1410,7 +1432,7 @@ __global__ void __launch_bounds__(512, 2) k_peel_loop(GraphView g, PeelView<CT> 
             unsigned long long now = globaltimer(), d = now - c->ph_last;
             c->ph_ns[ph] += d;
             c->ph_last = now;
-            if (ph >= 4 && P.round_ns && tr < P.round_cap) P.round_ns[tr] += (int64_t)d;
+            if ((ph == 4 || ph == 5) && P.round_ns && tr < P.round_cap) P.round_ns[tr] += (int64_t)d;
         }
     };
     // test of the barrier bound (ND_LIMIT_DROP_BLOCK): one block never arrives, so the others give
