@@ -146,6 +146,17 @@ ND_API int nd_ctx_set_allocator(nd_ctx *ctx, nd_alloc_fn alloc, nd_free_fn free_
 ND_API int nd_ctx_set_limits(nd_ctx *ctx, int64_t max_rounds, int64_t barrier_timeout_ns, int64_t count_limit,
                              int32_t flags);
 
+/* Per-(r,s) tuning of a context's decompositions (no counterpart in the paper), as chosen for
+ * a device and a workload by an autotuner:
+ *   heavy_work  length of an r-clique's driving list above which its Update runs on a whole block
+ *               in the heavy phase instead of one warp (0: the built-in threshold: 4096 for most
+ *               (r,s), 256 for (2,3), 96 for (2,4); (2,4) stages the common neighbourhood of a
+ *               warp's edge in shared memory and takes at most 96)
+ *   flags       ND_DENSE_BUCKETS and/or ND_CONTRACT_OFF, added to every nd_decompose of this (r,s)
+ *               on the context (also inside batches and the server)
+ * Errors: ND_EINVAL (NULL context, unsupported (r,s), negative threshold, other flags). */
+ND_API int nd_ctx_set_tuning(nd_ctx *ctx, int r, int s, int64_t heavy_work, int32_t flags);
+
 /* Destroy a context. All graphs created from it must have been freed (ND_EBUSY otherwise). */
 ND_API int nd_ctx_destroy(nd_ctx *ctx);
 

@@ -40,7 +40,7 @@ STATUS_NAMES = {0: "ND_OK", 1: "ND_EINVAL", 2: "ND_ENOMEM", 3: "ND_EOVERFLOW", 4
                 6: "ND_PENDING", 7: "ND_EINTERNAL", 8: "ND_ECUDA"}
 
 # every entry point declared in include/nd.h
-API = ["nd_ctx_create", "nd_ctx_set_allocator", "nd_ctx_set_limits", "nd_ctx_destroy", "nd_ctx_bytes_in_use", "nd_kernel_launches", "nd_last_error",
+API = ["nd_ctx_create", "nd_ctx_set_allocator", "nd_ctx_set_limits", "nd_ctx_set_tuning", "nd_ctx_destroy", "nd_ctx_bytes_in_use", "nd_kernel_launches", "nd_last_error",
        "nd_load_csr", "nd_graph_free", "nd_graph_size", "nd_orient", "nd_graph_reset", "nd_count", "nd_decompose",
        "nd_rounds", "nd_round_times", "nd_rcliques", "nd_batch_run", "nd_server_create", "nd_submit", "nd_poll", "nd_server_drain",
        "nd_server_destroy", "nd_kcore_noalloc"]
@@ -119,6 +119,7 @@ def lib() -> ctypes.CDLL:
         L.nd_ctx_create.argtypes = [ctypes.c_int, vp, ctypes.c_size_t, ctypes.POINTER(vp)]
         L.nd_ctx_set_allocator.argtypes = [vp, ALLOC_FN, FREE_FN, vp]
         L.nd_ctx_set_limits.argtypes = [vp, i64, i64, i64, i32]
+        L.nd_ctx_set_tuning.argtypes = [vp, ctypes.c_int, ctypes.c_int, i64, i32]
         L.nd_ctx_destroy.argtypes = [vp]
         L.nd_ctx_bytes_in_use.argtypes = [vp]
         L.nd_ctx_bytes_in_use.restype = ctypes.c_size_t
@@ -221,6 +222,12 @@ def nd_ctx_set_limits(ctx: Handle, max_rounds: int = 0, barrier_timeout_ns: int 
     """Round cap, grid-barrier wait bound, width-4 count limit and test flags of a context
     (nd.h: nd_ctx_set_limits); 0 keeps each default."""
     _check(lib().nd_ctx_set_limits(ctx.ptr, int(max_rounds), int(barrier_timeout_ns), int(count_limit), int(flags)))
+
+
+def nd_ctx_set_tuning(ctx: Handle, r: int, s: int, heavy_work: int = 0, flags: int = 0):
+    """Heavy-phase threshold and extra flags (ND_DENSE_BUCKETS, ND_CONTRACT_OFF) for every
+    decomposition of (r,s) on ctx (nd.h: nd_ctx_set_tuning); 0 / 0 restores the defaults."""
+    _check(lib().nd_ctx_set_tuning(ctx.ptr, int(r), int(s), int(heavy_work), int(flags)))
 
 
 def torch_allocator_hooks(device: int = 0):

@@ -117,6 +117,8 @@ static int read_back(nd_graph* g, const void* dptr, T* out, const char* what) {
     return ND_OK;
 }
 
+static bool rs_supported(int r, int s);
+
 // ------------------------------------------------------------------------------------
 // context
 
@@ -182,12 +184,23 @@ extern "C" int nd_ctx_set_limits(nd_ctx* ctx, int64_t max_rounds, int64_t barrie
     return ND_OK;
 }
 
+extern "C" int nd_ctx_set_tuning(nd_ctx* ctx, int r, int s, int64_t heavy_work, int32_t flags) {
+    if (!ctx) return nd_set_error(ND_EINVAL, "nd_ctx_set_tuning: NULL context");
+    if (!rs_supported(r, s)) return nd_set_error(ND_EINVAL, "nd_ctx_set_tuning: (r,s) = (%d,%d) is not supported", r, s);
+    if (heavy_work < 0 || (flags & ~(ND_DENSE_BUCKETS | ND_CONTRACT_OFF)))
+        return nd_set_error(ND_EINVAL, "nd_ctx_set_tuning: negative threshold or unknown flag");
+    ctx->tune_heavy[r * 8 + s] = heavy_work;
+    ctx->tune_flags[r * 8 + s] = flags;
+    return ND_OK;
+}
+
 extern "C" int nd_ctx_destroy(nd_ctx* ctx) {
     if (!ctx) return ND_OK;
     if (ctx->ngraphs.load() > 0) return nd_set_error(ND_EBUSY, "nd_ctx_destroy: graphs are still loaded");
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    if (ctx->stage) cudaFreeHost(ctx->stage);
     for (cudaStream_t x : ctx->cap_st)
         if (x) cudaStreamDestroy(x);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
@@ -758,6 +771,7 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
     P.ccol = P.cpos = P.clen = P.cprev = nullptr;
     P.bcnt = nullptr;
     P.bmax = 0;
+    P.heavy_work = c->tune_heavy[r * 8 + s];
     if (dense) {
         P.bcnt = (unsigned int*)bcnt.p;
         P.bmax = bmax;
@@ -915,6 +929,7 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
 
 int nd_decompose_dev(nd_graph* g, int r, int s, int count_width, int flags, PeelOut& po, nd_stats* st) {
     nd_ctx* c = g->ctx;
+    if (rs_supported(r, s)) flags |= c->tune_flags[r * 8 + s];
     nd_stats S;
     memset(&S, 0, sizeof(S));
     int64_t n_r = 0;

@@ -319,6 +319,9 @@ struct PeelView {
     // count is c, for c < bmax (the largest initial count + 1); NULL when off
     unsigned int* bcnt;
     int64_t bmax;
+    // driving-list length above which Update defers an r-clique to the heavy phase (0: the
+    // variant's built-in threshold)
+    int64_t heavy_work;
 };
 
 // ------------------------------------------------------------------------------------

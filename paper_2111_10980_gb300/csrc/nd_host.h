@@ -32,6 +32,11 @@ struct nd_ctx {
     int64_t barrier_ns = 0;
     int64_t count_limit = 0;
     int32_t limit_flags = 0;
+    void* stage = nullptr;  // pinned staging of batches (grown on demand)
+    size_t stage_bytes = 0;
+    // nd_ctx_set_tuning, indexed by r * 8 + s
+    int64_t tune_heavy[64] = {0};
+    int32_t tune_flags[64] = {0};
 };
 
 struct nd_graph {

@@ -1185,6 +1185,15 @@ __device__ __forceinline__ unsigned take_chunk(PeelCtl* c, unsigned chunk) {
     return __shfl_sync(0xffffffffu, i0, 0);
 }
 
+// the heavy-phase threshold of this decomposition: a tuned value if given (capped by what a warp's
+// stage holds for staged variants), else the variant's own
+template <typename U, typename CT>
+__device__ __forceinline__ int64_t heavy_limit(const PeelView<CT>& P) {
+    int64_t h = P.heavy_work > 0 ? P.heavy_work : heavy_work<U>::value;
+    if (is_staged<U>::value && h > heavy_work<U>::value) h = heavy_work<U>::value;
+    return h;
+}
+
 template <typename CT, typename U>
 __device__ void phase_update(const GraphView& g, const PeelView<CT>& P) {
     if (P.ctl->done) return;
@@ -1201,7 +1210,7 @@ __device__ void phase_update(const GraphView& g, const PeelView<CT>& P) {
         for (unsigned i = i0; i < i0 + chunk && i < E.nA; ++i) {
             int32_t R = E.A[i];
             if (lane == 0) unmark_a(P, R);
-            if (U::work(g, R) > heavy_work<U>::value) {
+            if (U::work(g, R) > heavy_limit<U>(P)) {
                 int queued = 0;
                 if (lane == 0) {
                     unsigned slot = atomicAdd(&P.ctl->nH, 1u);
@@ -1228,7 +1237,7 @@ __device__ void phase_update(const GraphView& g, const PeelView<CT>& P) {
             if (lane == 0) unmark_a(P, R);
             Prep q;
             int64_t n0 = U::prep(g, P, R, q);
-            if (n0 > heavy_work<U>::value) {
+            if (n0 > heavy_limit<U>(P)) {
                 int queued = 0;
                 if (lane == 0) {
                     unsigned slot = atomicAdd(&P.ctl->nH, 1u);

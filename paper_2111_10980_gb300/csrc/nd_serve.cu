@@ -53,20 +53,40 @@ double now_ms() {
     return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
 }
 
-// A request's CSR is checked on the host, in O(nnz log d), before it joins a union: rows
-// monotone, ids in range, rows strictly ascending, no self-loops, every (u,v) matched by (v,u).
-// A malformed request would otherwise shift into the union and send the kernels of every other
-// request of its group outside their arrays; this way it fails alone with ND_EINVAL.
-int check_request(const nd_request& q) {
+// Checks of a request's CSR on the host.
+//  * check_cheap, O(n + nnz), run while a batch copies the request into its union: rowptr starts
+//    at 0, never decreases and ends on an even count; every id lies in [0, n). After it, the
+//    union (ids shifted request by request) only ever points inside the request's own range, so
+//    the GPU validation of the union (ND_VALIDATE: sorted rows, no loops, symmetry) cannot read
+//    outside any array and any violation it finds lies inside one request.
+//  * check_request, O(nnz log d), everything the GPU validation checks; run only when the union
+//    of a batch fails validation, to find the requests at fault, which then fail alone with
+//    ND_EINVAL while the others run.
+int check_args(const nd_request& q) {
     if (q.n < 0 || !q.rowptr || !rs_ok(q.r, q.s)) return ND_EINVAL;
     const int64_t* rp = q.rowptr;
     if (rp[0] != 0 || rp[q.n] < 0 || (rp[q.n] > 0 && !q.col) || (rp[q.n] & 1)) return ND_EINVAL;
+    return ND_OK;
+}
+
+int check_cheap(const nd_request& q) {
+    if (check_args(q)) return ND_EINVAL;
+    const int64_t* rp = q.rowptr;
     for (int32_t u = 0; u < q.n; ++u)
         if (rp[u + 1] < rp[u]) return ND_EINVAL;
+    const int64_t nnz = rp[q.n];
+    uint32_t bad = 0;
+    for (int64_t p = 0; p < nnz; ++p) bad |= (uint32_t)q.col[p] >= (uint32_t)q.n;
+    return bad ? ND_EINVAL : ND_OK;
+}
+
+int check_request(const nd_request& q) {
+    if (check_cheap(q)) return ND_EINVAL;
+    const int64_t* rp = q.rowptr;
     for (int32_t u = 0; u < q.n; ++u) {
         for (int64_t p = rp[u]; p < rp[u + 1]; ++p) {
             int32_t v = q.col[p];
-            if (v < 0 || v >= q.n || v == u) return ND_EINVAL;
+            if (v == u) return ND_EINVAL;
             if (p > rp[u] && q.col[p - 1] >= v) return ND_EINVAL;
             const int32_t* row = q.col + rp[v];
             int64_t lo = 0, hi = rp[v + 1] - rp[v];
@@ -83,93 +103,192 @@ int check_request(const nd_request& q) {
     return ND_OK;
 }
 
-// Runs one union decomposition for the requests in idx (all with the same (r,s)).
-int run_group(nd_ctx* ctx, nd_request* const* reqs, const std::vector<int>& idx, nd_batch_stats* st) {
+// Union of the requests' CSRs on the device: the staged rows and neighbour lists are copied as
+// they are, then request k's row pointers are shifted by its first entry and its neighbour ids by
+// its first vertex (offsets voff / eoff, one block per request).
+__global__ void k_union_shift(int64_t* __restrict__ rp, int32_t* __restrict__ col, const int64_t* __restrict__ voff,
+                              const int64_t* __restrict__ eoff, int64_t count) {
+    for (int64_t k = blockIdx.x; k < count; k += gridDim.x) {
+        const int64_t v0 = voff[k], v1 = voff[k + 1], e0 = eoff[k], e1 = eoff[k + 1];
+        for (int64_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) rp[v] += e0;
+        const int32_t sh = (int32_t)v0;
+        for (int64_t p = e0 + threadIdx.x; p < e1; p += blockDim.x) col[p] += sh;
+    }
+}
+
+// Pinned staging memory of a context (grown on demand, freed with the context).
+void* stage_bytes(nd_ctx* ctx, size_t bytes) {
+    if (ctx->stage_bytes < bytes) {
+        if (ctx->stage) cudaFreeHost(ctx->stage);
+        ctx->stage = nullptr;
+        ctx->stage_bytes = 0;
+        size_t want = std::max(bytes, (size_t)1 << 20);
+        if (cudaMallocHost(&ctx->stage, want) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        ctx->stage_bytes = want;
+    }
+    return ctx->stage;
+}
+
+// Runs fn(i) for i in [0, count) on up to `threads` host threads (contiguous ranges).
+template <typename F>
+void parallel_for(int64_t count, int threads, F fn) {
+    if (count <= 0) return;
+    int t = (int)std::min<int64_t>(threads, count);
+    if (t <= 1) {
+        for (int64_t i = 0; i < count; ++i) fn(i);
+        return;
+    }
+    std::vector<std::thread> th;
+    for (int j = 0; j < t; ++j)
+        th.emplace_back([=] {
+            for (int64_t i = count * j / t; i < count * (j + 1) / t; ++i) fn(i);
+        });
+    for (auto& x : th) x.join();
+}
+
+int host_threads() {
+    unsigned h = std::thread::hardware_concurrency();
+    return (int)std::max(1u, std::min(8u, h ? h : 1u));
+}
+
+// Runs one union decomposition for the requests in idx (all with the same (r,s)). A request whose
+// CSR fails a check gets ND_EINVAL and is left out; the others run. peel_flags chooses how the
+// peeling loop is launched: nd_batch_run takes the cooperative persistent kernel (one launch for
+// the whole loop), the server's workers the loop graph, so that their batches share the SMs.
+int run_group(nd_ctx* ctx, nd_request* const* reqs, std::vector<int> idx, nd_batch_stats* st, int peel_flags) {
     int r = reqs[idx[0]]->r, s = reqs[idx[0]]->s;
-    int64_t total_n = 0, total_nnz = 0;
-    for (int i : idx) {
-        total_n += reqs[i]->n;
-        total_nnz += reqs[i]->rowptr[reqs[i]->n];
-    }
-    if (total_n > INT32_MAX) return nd_set_error(ND_EOVERFLOW, "batch: more than 2^31-1 vertices in one (r,s) group");
-    std::vector<int64_t> rp((size_t)total_n + 1);
-    std::vector<int32_t> col((size_t)std::max<int64_t>(total_nnz, 1));
-    std::vector<int64_t> voff(idx.size() + 1);
-    int64_t vo = 0, eo = 0;
-    for (size_t k = 0; k < idx.size(); ++k) {
-        const nd_request& q = *reqs[idx[k]];
-        voff[k] = vo;
-        for (int32_t v = 0; v < q.n; ++v) rp[vo + v] = eo + q.rowptr[v];
-        int64_t nnz = q.rowptr[q.n];
-        for (int64_t j = 0; j < nnz; ++j) col[eo + j] = q.col[j] + (int32_t)vo;
-        vo += q.n;
-        eo += nnz;
-    }
-    rp[total_n] = eo;
-    voff[idx.size()] = vo;
-    nd_graph* g = nullptr;
-    int rc = nd_load_csr(ctx, (int32_t)total_n, rp.data(), col.data(), 0, &g);
-    if (rc) return rc;
-    PeelOut po;
-    nd_stats S;
-    // the loop graph (not the cooperative kernel, which holds every SM) lets concurrent batches
-    // of the server overlap on the device
-    rc = nd_decompose_dev(g, r, s, 0, ND_PEEL_LOOP_GRAPH, po, &S);
-    std::vector<int64_t> off(idx.size() + 1);
-    if (!rc) {
-        DBuf dv, doff;
-        rc = nd_alloc(ctx, dv, sizeof(int64_t) * voff.size());
-        if (!rc) rc = nd_alloc(ctx, doff, sizeof(int64_t) * voff.size());
+    cudaStream_t stream = ctx->stream;
+    bool full_checks = false;  // set once the union of this group failed validation
+    // every pass either removes at least one request, switches to the full checks (once), or runs
+    // the decomposition and returns
+    while (!idx.empty()) {
+        const int64_t K = (int64_t)idx.size();
+        std::vector<int64_t> voff(K + 1), eoff(K + 1);
+        for (int64_t k = 0; k < K; ++k) {
+            voff[k + 1] = voff[k] + reqs[idx[k]]->n;
+            eoff[k + 1] = eoff[k] + reqs[idx[k]]->rowptr[reqs[idx[k]]->n];
+        }
+        const int64_t total_n = voff[K], total_nnz = eoff[K];
+        if (total_n > INT32_MAX) return nd_set_error(ND_EOVERFLOW, "batch: more than 2^31-1 vertices in one (r,s) group");
+        // stage rows and lists (pinned), checking each request on the way
+        size_t rp_bytes = sizeof(int64_t) * (total_n + 1), col_bytes = sizeof(int32_t) * total_nnz;
+        size_t col_at = (rp_bytes + 15) & ~(size_t)15;
+        char* stg = (char*)stage_bytes(ctx, col_at + col_bytes + 16);
+        if (!stg) return nd_set_error(ND_ENOMEM, "batch: pinned staging of %zu bytes failed", col_at + col_bytes);
+        int64_t* hrp = (int64_t*)stg;
+        int32_t* hcol = (int32_t*)(stg + col_at);
+        std::vector<int> bad(K, 0);
+        parallel_for(K, host_threads(), [&](int64_t k) {
+            const nd_request& q = *reqs[idx[k]];
+            bad[k] = full_checks ? check_request(q) : check_cheap(q);
+            if (bad[k]) return;
+            memcpy(hrp + voff[k], q.rowptr, sizeof(int64_t) * q.n);
+            int64_t nnz = q.rowptr[q.n];
+            if (nnz) memcpy(hcol + eoff[k], q.col, sizeof(int32_t) * nnz);
+        });
+        bool any_bad = false;
+        for (int64_t k = 0; k < K; ++k) any_bad |= bad[k] != 0;
+        if (any_bad) {
+            std::vector<int> keep;
+            for (int64_t k = 0; k < K; ++k) {
+                if (bad[k])
+                    reqs[idx[k]]->status = ND_EINVAL;
+                else
+                    keep.push_back(idx[k]);
+            }
+            idx.swap(keep);
+            continue;  // restage the others
+        }
+        hrp[total_n] = total_nnz;
+        DBuf drp, dcol, doffs;
+        int rc = nd_alloc(ctx, drp, rp_bytes);
+        if (!rc) rc = nd_alloc(ctx, dcol, std::max<size_t>(col_bytes, 4));
+        if (!rc) rc = nd_alloc(ctx, doffs, sizeof(int64_t) * 2 * (K + 1));
         if (!rc) {
-            cudaMemcpyAsync(dv.p, voff.data(), sizeof(int64_t) * voff.size(), cudaMemcpyHostToDevice, ctx->stream);
+            cudaMemcpyAsync(drp.p, hrp, rp_bytes, cudaMemcpyHostToDevice, stream);
+            if (col_bytes) cudaMemcpyAsync(dcol.p, hcol, col_bytes, cudaMemcpyHostToDevice, stream);
+            cudaMemcpyAsync(doffs.p, voff.data(), sizeof(int64_t) * (K + 1), cudaMemcpyHostToDevice, stream);
+            cudaMemcpyAsync((int64_t*)doffs.p + (K + 1), eoff.data(), sizeof(int64_t) * (K + 1), cudaMemcpyHostToDevice,
+                            stream);
+            int blocks = (int)std::min<int64_t>(K, (int64_t)nd_sm_count() * 8);
+            ND_K(k_union_shift<<<blocks, 256, 0, stream>>>((int64_t*)drp.p, (int32_t*)dcol.p, (const int64_t*)doffs.p,
+                                                          (const int64_t*)doffs.p + (K + 1), K));
+            rc = nd_check_launch("batch union");
+        }
+        nd_graph* g = nullptr;
+        if (!rc)
+            rc = nd_load_csr(ctx, (int32_t)total_n, (const int64_t*)drp.p, (const int32_t*)dcol.p,
+                             ND_PTR_DEVICE | ND_VALIDATE, &g);
+        nd_free(ctx, drp);
+        nd_free(ctx, dcol);
+        if (rc == ND_EINVAL && !full_checks) {
+            // the union is malformed inside some request: find it with the full host check
+            nd_free(ctx, doffs);
+            full_checks = true;
+            continue;
+        }
+        if (rc) {
+            nd_free(ctx, doffs);
+            return rc;
+        }
+        PeelOut po;
+        nd_stats S;
+        rc = nd_decompose_dev(g, r, s, 0, peel_flags, po, &S);
+        std::vector<int64_t> off(K + 1);
+        if (!rc) {
+            // canonical offset of each request's first r-clique: r = 1 its first vertex, r = 2 the
+            // edge base there, r = 3 the triangle base at that edge
             GraphView v = nd_view(g);
-            ND_K(k_gather_offsets<<<std::max<int64_t>(1, ((int64_t)voff.size() + 255) / 256), 256, 0, ctx->stream>>>(
-                v.ebase, v.tbase, (const int64_t*)dv.p, (int64_t)idx.size(), r, (int64_t*)doff.p));
+            ND_K(k_gather_offsets<<<std::max<int64_t>(1, (K + 1 + 255) / 256), 256, 0, stream>>>(
+                v.ebase, v.tbase, (const int64_t*)doffs.p, K, r, (int64_t*)doffs.p + (K + 1)));
             rc = nd_check_launch("batch offsets");
             if (!rc) {
-                cudaMemcpyAsync(off.data(), doff.p, sizeof(int64_t) * off.size(), cudaMemcpyDeviceToHost,
-                                ctx->stream);
+                cudaMemcpyAsync(off.data(), (int64_t*)doffs.p + (K + 1), sizeof(int64_t) * (K + 1),
+                                cudaMemcpyDeviceToHost, stream);
                 rc = nd_sync(ctx, "batch offsets");
             }
         }
-        nd_free(ctx, dv);
-        nd_free(ctx, doff);
-    }
-    if (!rc) {
-        std::vector<int32_t> core((size_t)std::max<int64_t>(S.n_r, 1));
-        if (S.n_r) {
-            cudaMemcpyAsync(core.data(), po.core.p, sizeof(int32_t) * S.n_r, cudaMemcpyDeviceToHost, ctx->stream);
-            rc = nd_sync(ctx, "batch results");
-        }
+        nd_free(ctx, doffs);
         if (!rc) {
-            for (size_t k = 0; k < idx.size(); ++k) {
-                nd_request& q = *reqs[idx[k]];
-                int64_t a = off[k], b = off[k + 1];
-                q.n_r = b - a;
-                if (q.core_out) {
-                    if (q.core_cap < q.n_r) {
-                        q.status = ND_EINVAL;
-                        continue;
-                    }
-                    memcpy(q.core_out, core.data() + a, sizeof(int32_t) * (b - a));
-                }
-                q.status = ND_OK;
+            int32_t* hcore = S.n_r ? (int32_t*)stage_bytes(ctx, sizeof(int32_t) * S.n_r) : nullptr;
+            if (S.n_r && !hcore) rc = nd_set_error(ND_ENOMEM, "batch: pinned staging of the results failed");
+            if (!rc && S.n_r) {
+                cudaMemcpyAsync(hcore, po.core.p, sizeof(int32_t) * S.n_r, cudaMemcpyDeviceToHost, stream);
+                rc = nd_sync(ctx, "batch results");
             }
-            if (st) {
-                st->n_r_total += S.n_r;
-                st->n_s_total += S.n_s;
-                st->rho_max = std::max<int64_t>(st->rho_max, S.rho);
+            if (!rc) {
+                parallel_for(K, host_threads(), [&](int64_t k) {
+                    nd_request& q = *reqs[idx[k]];
+                    int64_t a = off[k], b = off[k + 1];
+                    q.n_r = b - a;
+                    if (q.core_out) {
+                        if (q.core_cap < q.n_r) {
+                            q.status = ND_EINVAL;
+                            return;
+                        }
+                        if (b > a) memcpy(q.core_out, hcore + a, sizeof(int32_t) * (b - a));
+                    }
+                    q.status = ND_OK;
+                });
+                if (st) {
+                    st->n_r_total += S.n_r;
+                    st->n_s_total += S.n_s;
+                    st->rho_max = std::max<int64_t>(st->rho_max, S.rho);
+                }
             }
         }
+        nd_free(ctx, po.core);
+        nd_free(ctx, po.rnd);
+        nd_graph_free(g);
+        return rc;
     }
-    nd_free(ctx, po.core);
-    nd_free(ctx, po.rnd);
-    nd_graph_free(g);
-    return rc;
+    return ND_OK;
 }
 
-// checked: the requests already passed check_request (the server checks them in nd_submit)
-int batch_impl(nd_ctx* ctx, nd_request* const* reqs, int count, nd_batch_stats* st, bool checked = false) {
+int batch_impl(nd_ctx* ctx, nd_request* const* reqs, int count, nd_batch_stats* st, int peel_flags) {
     double t0 = now_ms();
     if (st) {
         memset(st, 0, sizeof(*st));
@@ -181,7 +300,7 @@ int batch_impl(nd_ctx* ctx, nd_request* const* reqs, int count, nd_batch_stats* 
     for (int i = 0; i < count; ++i) {
         nd_request& q = *reqs[i];
         q.n_r = 0;
-        q.status = checked ? ND_OK : check_request(q);
+        q.status = check_args(q);
         if (q.status) {
             if (!first_err) first_err = q.status;
             continue;
@@ -195,7 +314,7 @@ int batch_impl(nd_ctx* ctx, nd_request* const* reqs, int count, nd_batch_stats* 
         groups[gi].push_back(i);
     }
     for (auto& grp : groups) {
-        int rc = run_group(ctx, reqs, grp, st);
+        int rc = run_group(ctx, reqs, grp, st, peel_flags);
         if (rc) {
             for (int i : grp) reqs[i]->status = rc;
             if (!first_err) first_err = rc;
@@ -239,7 +358,7 @@ extern "C" int nd_batch_run(nd_ctx* ctx, nd_request* reqs, int32_t count, nd_bat
     cudaSetDevice(ctx->device);
     std::vector<nd_request*> ptrs(count);
     for (int i = 0; i < count; ++i) ptrs[i] = &reqs[i];
-    return batch_impl(ctx, ptrs.data(), count, st);
+    return batch_impl(ctx, ptrs.data(), count, st, 0);
 }
 
 // ------------------------------------------------------------------------------------
@@ -307,7 +426,7 @@ static void worker_loop(nd_server* sv, int w) {
         double t0 = now_ms();
         std::vector<nd_request*> reqs(batch.size());
         for (size_t i = 0; i < batch.size(); ++i) reqs[i] = &batch[i]->req;
-        batch_impl(ctx, reqs.data(), (int)reqs.size(), nullptr, true);
+        batch_impl(ctx, reqs.data(), (int)reqs.size(), nullptr, ND_PEEL_LOOP_GRAPH);
         double t1 = now_ms();
         {
             std::lock_guard<std::mutex> lk(sv->mu);
@@ -342,6 +461,14 @@ extern "C" int nd_server_create(nd_ctx* ctx, const nd_server_cfg* cfg, nd_server
             return rc;
         }
         nd_ctx_set_allocator(c, ctx->af, ctx->ff, ctx->user);
+        // the workers decompose with the server context's limits and tuning
+        c->max_rounds = ctx->max_rounds;
+        c->barrier_ns = ctx->barrier_ns;
+        c->count_limit = ctx->count_limit;
+        for (int i = 0; i < 64; ++i) {
+            c->tune_heavy[i] = ctx->tune_heavy[i];
+            c->tune_flags[i] = ctx->tune_flags[i];
+        }
         sv->wctx.push_back(c);
     }
     for (int w = 0; w < cfg->workers; ++w) sv->threads.emplace_back(worker_loop, sv, w);
@@ -351,7 +478,7 @@ extern "C" int nd_server_create(nd_ctx* ctx, const nd_server_cfg* cfg, nd_server
 
 extern "C" int nd_submit(nd_server* sv, const nd_request* req, uint64_t* ticket) {
     if (!sv || !req || !ticket) return nd_set_error(ND_EINVAL, "nd_submit: NULL argument");
-    if (check_request(*req)) return nd_set_error(ND_EINVAL, "nd_submit: malformed request");
+    if (check_args(*req)) return nd_set_error(ND_EINVAL, "nd_submit: malformed request");
     Ticket* t = new Ticket();
     t->req = *req;
     t->req.status = ND_PENDING;

@@ -81,26 +81,51 @@ def _fake_stats(rs_list):
     return [st]
 
 
+SUMS = {"sum_deg": 800, "edge_min_deg": 900, "edge_dplus": 1100, "n3": 1000, "tri_min_deg": 2000,
+        "tri_dplus_last": 700}
+
+
+class _G:
+    n, m = 100, 400
+
+
+def test_byte_models_written_out():
+    """The method's lower-bound model on hand-set sums: (3,4) peel = 4 sum_t min deg + C(4,3) n_4
+    listings x 3 other triangles x 5 B + 2w per decrement + 8 B per triangle of A; count = 4 sum_e
+    (d+(u) + d+(v)) + 4 sum_t d+(last) + 2w per count."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    st = _fake_stats([(3, 4)])[0][(3, 4)]
+    cm, pm, ci, pi = bench.byte_models(3, 4, st, SUMS, _G())
+    assert pm == 4 * 2000 + 4 * 5000 * 3 * 5 + 8 * 12000 + 8 * 1000
+    assert cm == 4 * 1100 + 4 * 700 + 8 * 1000
+    assert ci == 64 * 1000 + 32 * 5000 and pi == 72 * 1000 + 28 * 5000 + 8 * 12000
+    cm, pm, _, _ = bench.byte_models(2, 3, _fake_stats([(2, 3)])[0][(2, 3)], SUMS, _G())
+    assert pm == 4 * 900 + 3 * 5000 * 2 * 5 + 8 * 12000 + 8 * 1000 and cm == 4 * 1100 + 8 * 1000
+    cm, pm, _, _ = bench.byte_models(1, 2, _fake_stats([(1, 2)])[0][(1, 2)], SUMS, _G())
+    assert cm == 8 * 101 and pm == 4 * 800 + 2 * 5000 * 1 * 5 + 8 * 12000 + 8 * 1000
+
+
 def test_roofline_models_and_traffic_gate(monkeypatch):
-    """Every benchmarked (r,s) has a nonzero byte model; the ncu traffic figure is reported only
+    """Every benchmarked (r,s) has nonzero byte models; the ncu traffic figure is reported only
     while the library sources match the fingerprint the capture was taken on."""
     sys.path.insert(0, ROOT)
     import bench
 
-    class G:
-        n, m = 100, 400
-
-    for name, rs_list in [("rmat20", [(2, 3), (3, 4)]), ("cl4m", [(3, 4), (2, 4)])]:
-        wl = {"name": name, "rs": rs_list}
-        top = bench.roofline(wl, _fake_stats(rs_list), G())
+    for name, rs_list in [("rmat20", [(2, 3), (3, 4)]), ("cl4m", [(3, 4), (2, 4)]),
+                          ("rmat_dense", [(2, 5), (3, 5)])]:
+        top = bench.roofline(name, rs_list, _fake_stats(rs_list), _G(), SUMS)
         for e in [top] + top["others"]:
-            assert e["algorithmic_bytes_per_launch"] > 0, e["kernel"]
+            assert e["algorithmic_bytes_per_launch"] > 0 and e["implementation_bytes_per_launch"] > 0, e["kernel"]
             assert e["unit"] == "GB/s" and e["bound"] == "hbm"
-    fp = next(iter(bench.NCU_TRAFFIC))
-    wl = {"name": "rmat20", "rs": [(2, 3), (3, 4)]}
-    monkeypatch.setattr(bench, "sources_fingerprint", lambda: fp)
-    top = bench.roofline(wl, _fake_stats(wl["rs"]), G())
-    assert top["traffic"] == bench.NCU_TRAFFIC[fp][("rmat20", top["kernel"])]
+            assert abs(e["frac"] - e["achieved"] / e["peak"]) < 1e-12
+    table = {"f" * 16: {("rmat20", "k_peel_loop(3,4)"): 1.5e9, ("rmat20", "k_peel_loop(2,3)"): 2.5e8}}
+    monkeypatch.setattr(bench, "NCU_TRAFFIC", table)
+    monkeypatch.setattr(bench, "sources_fingerprint", lambda: "f" * 16)
+    rs = [(2, 3), (3, 4)]
+    top = bench.roofline("rmat20", rs, _fake_stats(rs), _G(), SUMS)
+    assert top["traffic"] == table["f" * 16].get(("rmat20", top["kernel"]))
     monkeypatch.setattr(bench, "sources_fingerprint", lambda: "0" * 16)
-    top = bench.roofline(wl, _fake_stats(wl["rs"]), G())
+    top = bench.roofline("rmat20", rs, _fake_stats(rs), _G(), SUMS)
     assert top["traffic"] is None and all(o["traffic"] is None for o in top["others"])

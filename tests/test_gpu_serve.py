@@ -221,8 +221,10 @@ def test_server_on_the_serve_pool_against_oracle_and_alone(nd, ctx, serve_items)
 
 def test_malformed_requests_fail_alone(nd, ctx):
     """A request whose CSR breaks an invariant (an id out of range, an unsorted row, a
-    self-loop, a missing reverse entry) is rejected on the host with ND_EINVAL, in a batch and
-    by the server, while the well-formed requests beside it still get the oracle's result."""
+    self-loop, a missing reverse entry) fails alone with ND_EINVAL, in a batch and in the
+    server, while the well-formed requests beside it still get the oracle's result. Ids out of
+    range are caught on the host before the union is built; the other faults by the GPU
+    validation of the union, after which the host checks each request in full."""
     good = [gg.chung_lu(300, 10.0, 2.2, seed=71), gg.rmat(8, 8, 0.57, 0.19, 0.19, seed=72)]
     base = gg.chung_lu(200, 8.0, 2.2, seed=73)
     row = int(np.argmax(np.diff(base.rowptr)))
@@ -258,16 +260,22 @@ def test_malformed_requests_fail_alone(nd, ctx):
     assert np.array_equal(outs[0][:n_r[0]], orc.decompose(good[0], 2, 3).core)
     assert np.array_equal(outs[-2][:n_r[-2]], orc.decompose(good[1], 2, 3).core)
     assert np.array_equal(outs[-1][:n_r[-1]], orc.decompose(good[1], 3, 4).core)
-    sv = nd.nd_server_create(ctx, workers=2, max_batch=8)
+    # the server accepts them (nd_submit checks only the arguments, in O(1)) and they fail with
+    # ND_EINVAL in their batch, next to a good request that is served
+    sv = nd.nd_server_create(ctx, workers=1, max_batch=8)
     try:
-        for c in bads:
-            with pytest.raises(nd.NdError) as ei:
-                sv.submit(base.rowptr, c, 2, 3, np.zeros(base.m, np.int32))
-            assert ei.value.code == nd.ND_EINVAL
         out = np.zeros(good[0].m, np.int32)
+        tickets = [sv.submit(base.rowptr, c, 2, 3, np.zeros(base.m, np.int32)) for c in bads]
         t = sv.submit(good[0].rowptr, good[0].col, 2, 3, out)
         sv.drain()
+        for tb in tickets:
+            assert sv.poll(tb)[0] == nd.ND_EINVAL
         assert sv.poll(t)[0] == nd.ND_OK
         assert np.array_equal(out, orc.decompose(good[0], 2, 3).core)
+        bad_rp = base.rowptr.copy()
+        bad_rp[0] = 1
+        with pytest.raises(nd.NdError) as ei:
+            sv.submit(bad_rp, base.col, 2, 3, np.zeros(base.m, np.int32))
+        assert ei.value.code == nd.ND_EINVAL
     finally:
         sv.close()
