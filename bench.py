@@ -103,10 +103,14 @@ def parse_args():
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-pool", type=int, default=256)
     ap.add_argument("--serve-workers", type=int, default=4)
+    ap.add_argument("--serve-batch", type=int, default=256, help="most requests merged into one server batch")
+    ap.add_argument("--serve-mode", choices=["loop_graph", "persistent"], default="loop_graph",
+                    help="how the server's workers launch a batch's peeling loop")
     ap.add_argument("--serve-queue", type=int, default=4096,
                     help="requests waiting for admission beyond which new ones are rejected (both arms)")
     ap.add_argument("--serve-drain", type=float, default=30.0,
                     help="seconds after the last arrival that each arm may take to finish its queue")
+    ap.add_argument("--no-serial", action="store_true", help="serve workload: skip the serial arm")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-configs", action="store_true", help="skip the other workloads in the default run")
@@ -688,7 +692,8 @@ def _latency_summary(lat_ms, censored_ms, span_s, offered, rejected):
             "offered": int(offered), "span_s": span_s}
 
 
-def serve_result(nd, seconds, rate, pool_size, workers, queue_cap, drain_s, local, seed=5):
+def serve_result(nd, seconds, rate, pool_size, workers, queue_cap, drain_s, local, seed=5, max_batch=256,
+                 mode="loop_graph", serial=True):
     """A Poisson stream of requests against the continuous-batching server, and the same trace served
     live one request at a time on the same GPU (load + decompose + copy out, FIFO). Both arms admit
     at most queue_cap waiting requests and reject the rest; both stop drain_s after the last
@@ -717,7 +722,8 @@ def serve_result(nd, seconds, rate, pool_size, workers, queue_cap, drain_s, loca
     outs = {key: np.empty(max(v[0], 1), np.int32) for key, v in info.items()}
 
     # --- the server
-    sv = nd.nd_server_create(ctx, workers=workers, max_batch=256, queue_cap=queue_cap)
+    sv = nd.nd_server_create(ctx, workers=workers, max_batch=max_batch, queue_cap=queue_cap,
+                             flags=nd.ND_PEEL_PERSISTENT if mode == "persistent" else nd.ND_PEEL_LOOP_GRAPH)
     lat, units_done = [], [0]
     pending = {}
     lock = threading.Lock()
@@ -767,7 +773,15 @@ def serve_result(nd, seconds, rate, pool_size, workers, queue_cap, drain_s, loca
     sv.close()  # finishes what was admitted (not timed)
     server = _latency_summary(lat, censored, now, arrivals.size, rejected)
     server["s_cliques_per_s"] = units_done[0] / max(now, 1e-9)
-    server["workers"] = workers
+    server.update(workers=workers, max_batch=max_batch, peel_mode=mode)
+    out = {"metric": "served (r,s) requests/sec, p50/p99 latency", "rate_per_s": rate, "seconds": seconds,
+           "requests": int(arrivals.size), "pool_graphs": len(pool), "queue_cap": queue_cap, "drain_s": drain_s,
+           "desc": "Poisson arrivals; graphs Chung-Lu or R-MAT, m log-uniform [1e2, 1e6], (r,s) uniform over "
+                   "(2,3),(3,4),(2,4); graphs pre-generated in host memory",
+           "server": server}
+    if not serial:
+        nd.nd_ctx_destroy(ctx)
+        return out
 
     # --- serial plain-GPU handling of the same trace, live
     q = collections.deque()
@@ -819,11 +833,8 @@ def serve_result(nd, seconds, rate, pool_size, workers, queue_cap, drain_s, loca
     serial = _latency_summary(lat2, censored2, now, arrivals.size, rejected2)
     serial["s_cliques_per_s"] = units2[0] / max(now, 1e-9)
     nd.nd_ctx_destroy(ctx)
-    return {"metric": "served (r,s) requests/sec, p50/p99 latency", "rate_per_s": rate, "seconds": seconds,
-            "requests": int(arrivals.size), "pool_graphs": len(pool), "queue_cap": queue_cap, "drain_s": drain_s,
-            "desc": "Poisson arrivals; graphs Chung-Lu or R-MAT, m log-uniform [1e2, 1e6], (r,s) uniform over "
-                    "(2,3),(3,4),(2,4); graphs pre-generated in host memory",
-            "server": server, "serial_plain_gpu": serial}
+    out["serial_plain_gpu"] = serial
+    return out
 
 
 # ------------------------------------------------------------------------------------------
@@ -876,7 +887,8 @@ def main():
         return 0
     if args.workload == "serve":
         line = serve_result(nd, args.serve_seconds, args.serve_rate, args.serve_pool, args.serve_workers,
-                            args.serve_queue, args.serve_drain, local, seed=5 + rank)
+                            args.serve_queue, args.serve_drain, local, seed=5 + rank, max_batch=args.serve_batch,
+                            mode=args.serve_mode, serial=not args.no_serial)
         line.update(value=line["server"]["requests_per_s"], unit="requests/s", n_gpus=1, steps=1, warmup=0,
                     higher_is_better=True, scaling="weak", vs_baseline=None, dtype="int32", data="synthetic",
                     config={"workload": "serve", "rate_per_s": args.serve_rate, "seconds": args.serve_seconds})
@@ -943,7 +955,9 @@ def main():
         for key, fn in (("batched_4096", lambda: batch_result(nd, args.batch_graphs, args.config_steps, 1, local)),
                         ("served_2000_per_s", lambda: serve_result(nd, args.serve_seconds, args.serve_rate,
                                                                    args.serve_pool, args.serve_workers,
-                                                                   args.serve_queue, args.serve_drain, local))):
+                                                                   args.serve_queue, args.serve_drain, local,
+                                                                   max_batch=args.serve_batch,
+                                                                   mode=args.serve_mode))):
             try:
                 cfg[key] = fn()
             except Exception as e:

@@ -273,7 +273,9 @@ typedef struct nd_server_cfg {
     int32_t workers;       /* batches running on the device at once, each on its own stream (>= 1) */
     int32_t max_batch;     /* most requests merged into one batch (>= 1) */
     int32_t queue_cap;     /* most requests waiting for admission; nd_submit returns ND_EBUSY beyond */
-    int32_t pad;
+    int32_t flags;         /* how a worker launches a batch's peeling loop: 0 or ND_PEEL_LOOP_GRAPH (a CUDA
+                              graph per batch; the workers' batches share the SMs), ND_PEEL_PERSISTENT
+                              (one cooperative kernel per batch, holding every SM; batches take turns) */
 } nd_server_cfg;
 
 typedef struct nd_result {

@@ -85,7 +85,7 @@ class nd_batch_stats(ctypes.Structure):
 
 class nd_server_cfg(ctypes.Structure):
     _fields_ = [("mem_budget", ctypes.c_size_t), ("workers", ctypes.c_int32), ("max_batch", ctypes.c_int32),
-                ("queue_cap", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("queue_cap", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
 
 class nd_result(ctypes.Structure):
@@ -431,8 +431,8 @@ class Server:
     """A continuous-batching server (nd.h: nd_server_create / nd_submit / nd_poll)."""
 
     def __init__(self, ctx: Handle, mem_budget: int = 0, workers: int = 2, max_batch: int = 64,
-                 queue_cap: int = 1 << 20):
-        cfg = nd_server_cfg(mem_budget, workers, max_batch, queue_cap, 0)
+                 queue_cap: int = 1 << 20, flags: int = 0):
+        cfg = nd_server_cfg(mem_budget, workers, max_batch, queue_cap, flags)
         out = ctypes.c_void_p()
         _check(lib().nd_server_create(ctx.ptr, ctypes.byref(cfg), ctypes.byref(out)))
         self.ptr = out
@@ -465,8 +465,8 @@ class Server:
 
 
 def nd_server_create(ctx: Handle, mem_budget: int = 0, workers: int = 2, max_batch: int = 64,
-                     queue_cap: int = 1 << 20) -> Server:
-    return Server(ctx, mem_budget, workers, max_batch, queue_cap)
+                     queue_cap: int = 1 << 20, flags: int = 0) -> Server:
+    return Server(ctx, mem_budget, workers, max_batch, queue_cap, flags)
 
 
 def nd_submit(sv: Server, rowptr, col, r, s, core_out) -> int:

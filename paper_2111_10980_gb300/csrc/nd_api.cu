@@ -700,7 +700,7 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
         ND_TRY(read_back(g, g->scal.p, &mx, "peel setup"));
         bmax = (int64_t)mx + 1;
     }
-    DBuf ctl, A0, A1, N0, N1, L0, L1, H, rs, rl, rt, etr, hsc, abits, ccol, cpos, clen, cprev, bcnt;
+    DBuf ctl, A0, A1, N0, N1, L0, L1, H, rs, rl, rt, etr, hsc, abits, ccol, cpos, clen, cprev, bcnt, hcnt, hpre;
     if ((rc = nd_alloc(c, ctl, sizeof(PeelCtl))) || (rc = nd_alloc(c, A0, 4 * cap)) || (rc = nd_alloc(c, A1, 4 * cap)) ||
         (rc = nd_alloc(c, N0, 4 * cap)) || (rc = nd_alloc(c, N1, 4 * cap)) || (rc = nd_alloc(c, L0, 4 * cap)) ||
         (rc = nd_alloc(c, L1, 4 * cap)) || (rc = nd_alloc(c, H, 4 * hcap)) || (rc = nd_alloc(c, rs, 8 * rcap)) ||
@@ -711,9 +711,10 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
                       (rc = nd_alloc(c, cpos, 4 * std::max<int64_t>(g->nnz, 1))) ||
                       (rc = nd_alloc(c, clen, 4 * std::max<int64_t>(g->n, 1))) ||
                       (rc = nd_alloc(c, cprev, 4 * std::max<int64_t>(g->n, 1))))) ||
-        (dense && (rc = nd_alloc(c, bcnt, 4 * std::max<int64_t>(bmax, 1))))) {
+        (dense && (rc = nd_alloc(c, bcnt, 4 * std::max<int64_t>(bmax, 1)))) ||
+        (staged && ((rc = nd_alloc(c, hcnt, 4 * (hslices + 1))) || (rc = nd_alloc(c, hpre, 8 * (hslices + 1)))))) {
         for (DBuf* b : {&ctl, &A0, &A1, &N0, &N1, &L0, &L1, &H, &rs, &rl, &rt, &etr, &hsc, &abits, &ccol, &cpos, &clen,
-                        &cprev, &bcnt})
+                        &cprev, &bcnt, &hcnt, &hpre})
             nd_free(c, *b);
         return rc;
     }
@@ -730,6 +731,8 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
     P.H = (int32_t*)H.p;
     P.hcap = (uint32_t)hcap;
     P.hscratch = (int32_t*)hsc.p;
+    P.hcnt = staged ? (int32_t*)hcnt.p : nullptr;
+    P.hpre = staged ? (int64_t*)hpre.p : nullptr;
     P.hstage = hstage;
     P.hslices = (int32_t)hslices;
     // id-order rebuilds of A pay off for triangles (their lists are long); edges and vertices
@@ -922,7 +925,7 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
         }
     }
     for (DBuf* b : {&ctl, &A0, &A1, &N0, &N1, &L0, &L1, &H, &rs, &rl, &rt, &etr, &hsc, &abits, &ccol, &cpos, &clen,
-                    &cprev, &bcnt})
+                    &cprev, &bcnt, &hcnt, &hpre})
         nd_free(c, *b);
     return rc;
 }

@@ -233,7 +233,7 @@ struct PeelCtl {
     int32_t lmat;       // 0: L is implicitly 0..n_r-1
     int32_t heavy;      // persistent kernel: this round has a heavy phase (set by a serial step)
     int32_t sorta;      // persistent kernel: this round rebuilds A in id order (set by a serial step)
-    int32_t pad1;
+    int32_t heavy_split;// persistent kernel, (2,4): this round's heavy phase is split over the grid
     int64_t k;          // current level
     int64_t hi;         // bucket window: N holds every unpeeled r-clique with count < hi
     int64_t finished;   // r-cliques peeled so far
@@ -288,6 +288,10 @@ struct PeelView {
     int32_t* hscratch;
     int64_t hstage;
     int32_t hslices;
+    // (2,4) heavy phase split over the grid (persistent kernel): per slice the number of staged
+    // vertices, and the candidate pairs of each heavy edge turned into offsets (hslices + 1)
+    int32_t* hcnt;
+    int64_t* hpre;
     // membership bitmap of A (NULL: never sorted) and the |A| from which a round sorts A
     uint32_t* abits;
     uint32_t sort_min;

@@ -909,10 +909,11 @@ struct Upd24 {
         __syncwarp();
     }
 
-    // One block (the heavy phase); the stage is the block's global scratch slice. Every thread of
-    // the block calls it.
-    __device__ static void run_block(const GraphView& g, const RoundEnv<CT>& E, int32_t R, UpdCounters& k,
-                                     const Stage24& st) {
+    // One block stages I of edge R in its global scratch slice and turns the out-degrees into the
+    // exclusive prefix of the candidate pairs; returns the number of pairs (the same in every
+    // thread) and sets cnt_out to |I|. Every thread of the block calls it.
+    __device__ static int32_t stage_block(const GraphView& g, const RoundEnv<CT>& E, int32_t R, const Stage24& st,
+                                          int& cnt_out) {
         __shared__ int32_t s_tot[kMaxWarpsPerBlock];
         __shared__ int32_t s_cnt, s_carry;
         int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -973,6 +974,17 @@ struct Upd24 {
         }
         __syncthreads();
         int32_t total = s_carry;
+        cnt_out = cnt;
+        __syncthreads();
+        return total;
+    }
+
+    // One block (the heavy phase); the stage is the block's global scratch slice. Every thread of
+    // the block calls it.
+    __device__ static void run_block(const GraphView& g, const RoundEnv<CT>& E, int32_t R, UpdCounters& k,
+                                     const Stage24& st) {
+        int cnt = 0;
+        int32_t total = stage_block(g, E, R, st, cnt);
         for (int32_t p = threadIdx.x; p < total; p += blockDim.x) pair(g, E, R, st, cnt, p, k);
         __syncthreads();
     }
@@ -1284,6 +1296,53 @@ __device__ void phase_update_heavy(const GraphView& g, const PeelView<CT>& P) {
     add_counters(P.ctl, k);
 }
 
+// (2,4) heavy phase split over the grid (persistent kernel, when the round's heavy edges fit the
+// scratch slices): first every heavy edge is staged by one block into its own slice (I, its edge
+// ids and out-list bounds, the prefix of the candidate pairs); then, after a barrier whose serial
+// step turns the per-edge pair totals into offsets, every thread of the grid takes candidate pairs
+// of any heavy edge. A round whose few heavy edges used to occupy a few blocks spreads them over
+// all of them.
+template <typename CT, typename U>
+__device__ void phase_heavy_stage(const GraphView& g, const PeelView<CT>& P) {
+    if (P.ctl->done) return;
+    unsigned nH = clampn(P.ctl->nH, P.hcap);
+    RoundEnv<CT> E = round_env(P);
+    const int64_t c = P.hstage + 1;
+    for (unsigned b = blockIdx.x; b < nH; b += gridDim.x) {
+        int32_t* base = P.hscratch + (int64_t)b * 5 * c;
+        Stage24 stg{base, base + c, base + 2 * c, base + 3 * c, base + 4 * c};
+        int cnt = 0;
+        int32_t total = U::stage_block(g, E, P.H[b], stg, cnt);
+        if (threadIdx.x == 0) {
+            P.hcnt[b] = cnt;
+            P.hpre[b] = total;
+        }
+    }
+}
+
+template <typename CT, typename U>
+__device__ void phase_heavy_pairs(const GraphView& g, const PeelView<CT>& P) {
+    if (P.ctl->done) return;
+    unsigned nH = clampn(P.ctl->nH, P.hcap);
+    RoundEnv<CT> E = round_env(P);
+    UpdCounters k;
+    const int64_t c = P.hstage + 1, T = P.hpre[nH];
+    for (int64_t p = gthread(); p < T; p += nthreads()) {
+        unsigned lo = 0, hi = nH;  // the last edge whose offset is <= p
+        while (hi - lo > 1) {
+            unsigned mid = (lo + hi) >> 1;
+            if (P.hpre[mid] <= p)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        int32_t* base = P.hscratch + (int64_t)lo * 5 * c;
+        Stage24 stg{base, base + c, base + 2 * c, base + 3 * c, base + 4 * c};
+        U::pair(g, E, P.H[lo], stg, P.hcnt[lo], (int32_t)(p - P.hpre[lo]), k);
+    }
+    add_counters(P.ctl, k);
+}
+
 template <typename CT, typename U>
 __global__ void k_update(GraphView g, PeelView<CT> P) { phase_update<CT, U>(g, P); }
 template <typename CT, typename U>
@@ -1413,6 +1472,7 @@ struct CtlUnlessHeavy {
         // the blocks branch on `heavy`, which only serial steps write: nH itself may already be
         // growing in the next round's update by the time a slow block looks
         c->heavy = c->nH != 0;
+        c->heavy_split = c->heavy && P->hpre && c->nH <= (unsigned)P->hslices;
         if (!c->heavy) {
             ctl_step(c, P->round_size, P->round_level, P->round_cap);
             decide_sort(c, P);
@@ -1423,6 +1483,23 @@ struct CtlUnlessHeavy {
 struct PickSerial {
     PeelCtl* c;
     __device__ void operator()() const { refill_pick_serial(c); }
+};
+
+// (2,4) heavy phase split over the grid: the pair totals of the staged heavy edges become offsets
+template <typename CT>
+struct HeavyScan {
+    PeelCtl* c;
+    const PeelView<CT>* P;
+    __device__ void operator()() const {
+        unsigned nH = c->nH;
+        long long run = 0;
+        for (unsigned b = 0; b < nH; ++b) {
+            long long v = P->hpre[b];
+            P->hpre[b] = run;
+            run += v;
+        }
+        P->hpre[nH] = run;
+    }
 };
 
 // One round: [advance: min over N; (refill: compact + min, histogram, pick, select); select A]
@@ -1485,6 +1562,16 @@ __global__ void __launch_bounds__(512, 2) k_peel_loop(GraphView g, PeelView<CT> 
         if (!grid_barrier(c, target, CtlUnlessHeavy<CT>{c, &P})) return;
         book(4);
         if (c->heavy) {
+            if constexpr (is_staged<U>::value) {
+                if (c->heavy_split) {  // written only by serial steps
+                    phase_heavy_stage<CT, U>(g, P);
+                    if (!grid_barrier(c, target, HeavyScan<CT>{c, &P})) return;
+                    phase_heavy_pairs<CT, U>(g, P);
+                    if (!grid_barrier(c, target, CtlSerial<CT>{c, &P})) return;
+                    book(5);
+                    continue;
+                }
+            }
             phase_update_heavy<CT, U>(g, P);
             if (!grid_barrier(c, target, CtlSerial<CT>{c, &P})) return;
             book(5);

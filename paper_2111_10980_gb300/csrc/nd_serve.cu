@@ -426,7 +426,8 @@ static void worker_loop(nd_server* sv, int w) {
         double t0 = now_ms();
         std::vector<nd_request*> reqs(batch.size());
         for (size_t i = 0; i < batch.size(); ++i) reqs[i] = &batch[i]->req;
-        batch_impl(ctx, reqs.data(), (int)reqs.size(), nullptr, ND_PEEL_LOOP_GRAPH);
+        batch_impl(ctx, reqs.data(), (int)reqs.size(), nullptr,
+                   sv->cfg.flags == ND_PEEL_PERSISTENT ? ND_PEEL_PERSISTENT : ND_PEEL_LOOP_GRAPH);
         double t1 = now_ms();
         {
             std::lock_guard<std::mutex> lk(sv->mu);
@@ -449,6 +450,8 @@ extern "C" int nd_server_create(nd_ctx* ctx, const nd_server_cfg* cfg, nd_server
     if (!ctx || !cfg || !out) return nd_set_error(ND_EINVAL, "nd_server_create: NULL argument");
     if (cfg->workers < 1 || cfg->max_batch < 1 || cfg->queue_cap < 1)
         return nd_set_error(ND_EINVAL, "nd_server_create: workers, max_batch and queue_cap must be >= 1");
+    if (cfg->flags != 0 && cfg->flags != ND_PEEL_LOOP_GRAPH && cfg->flags != ND_PEEL_PERSISTENT)
+        return nd_set_error(ND_EINVAL, "nd_server_create: flags must be 0, ND_PEEL_LOOP_GRAPH or ND_PEEL_PERSISTENT");
     nd_server* sv = new nd_server();
     sv->ctx = ctx;
     sv->cfg = *cfg;
