@@ -85,6 +85,12 @@ WORKLOADS = {
     ),
 }
 
+# The density sweep of Fig. 13: R-MAT with a=0.5, b=c=0.1 (d=0.3), duplicate edges removed, at
+# several edge factors, for (2,3), (3,4) and (4,5).
+SWEEP_SCALE = 15
+SWEEP_EDGE_FACTORS = [4, 8, 16, 32]
+SWEEP_RS = [(2, 3), (3, 4), (4, 5)]
+
 
 def units_of(r: int, s: int, n_s: int) -> int:
     """s-cliques of Algorithm 2: each counted once, then re-listed once per member r-clique."""
@@ -97,7 +103,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch", "serve"], default="rmat20")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch", "serve", "sweep"], default="rmat20")
     ap.add_argument("--batch-graphs", type=int, default=4096)
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
@@ -603,6 +609,25 @@ def secondary(nd, name, steps, local, flush, stream, flags=0):
             "per_rs": per_rs_summary(stats, wl["rs"]), "roofline": roof, "generate_s": gen_s}
 
 
+def density_sweep(nd, local, flush, stream, steps=2):
+    """Fig. 13's R-MAT density sweep: s-cliques/s of (2,3), (3,4), (4,5) as the edge factor grows."""
+    out = []
+    for ef in SWEEP_EDGE_FACTORS:
+        g = gg.rmat(SWEEP_SCALE, ef, 0.5, 0.1, 0.1, seed=7)
+        res = Resident(nd, g, local, stream)
+        row = {"scale": SWEEP_SCALE, "edge_factor": ef, "n": g.n, "m": g.m, "rs": {}}
+        for r, s in SWEEP_RS:
+            per_step, t_ms, _, _, _ = res.timed([(r, s)], 0, 0, steps, 1, flush)
+            st = per_step[-1][(r, s)]
+            row["rs"][f"({r},{s})"] = {"n_r": st["n_r"], "n_s": st["n_s"], "rho": st["rho"], "max_core": st["max_core"],
+                                       "ms": t_ms / steps, "s_cliques_per_s": units_of(r, s, st["n_s"]) * steps /
+                                       (t_ms / 1000.0)}
+        res.close()
+        out.append(row)
+    return {"desc": f"R-MAT scale {SWEEP_SCALE}, a=0.5 b=0.1 c=0.1, edge factors {SWEEP_EDGE_FACTORS}, duplicates "
+                    "removed; one step = index + count + peel of one (r,s)", "points": out}
+
+
 # ------------------------------------------------------------------------------------------
 # batched and served workloads
 
@@ -885,6 +910,15 @@ def main():
         if rank == 0:
             print(json.dumps(line), flush=True)
         return 0
+    if args.workload == "sweep":
+        stream = torch.cuda.Stream(device=local)
+        flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=f"cuda:{local}")
+        line = density_sweep(nd, local, flush, stream, steps=args.steps)
+        line.update(metric="(r,s) s-cliques/sec over an R-MAT density sweep", n_gpus=1, data="synthetic",
+                    config={"workload": "sweep"})
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return 0
     if args.workload == "serve":
         line = serve_result(nd, args.serve_seconds, args.serve_rate, args.serve_pool, args.serve_workers,
                             args.serve_queue, args.serve_drain, local, seed=5 + rank, max_batch=args.serve_batch,
@@ -952,6 +986,10 @@ def main():
                 cfg[key] = secondary(nd, name, args.config_steps if name == "cl4m" else 20, local, flush, stream)
             except Exception as e:  # report it, keep the main line
                 cfg[key] = {"error": repr(e)}
+        try:
+            cfg["rmat_density_sweep"] = density_sweep(nd, local, flush, stream)
+        except Exception as e:
+            cfg["rmat_density_sweep"] = {"error": repr(e)}
         for key, fn in (("batched_4096", lambda: batch_result(nd, args.batch_graphs, args.config_steps, 1, local)),
                         ("served_2000_per_s", lambda: serve_result(nd, args.serve_seconds, args.serve_rate,
                                                                    args.serve_pool, args.serve_workers,

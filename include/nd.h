@@ -27,8 +27,9 @@
  *     lexicographically by their ascending tuple of vertex ids. r = 1: vertex id; r = 2:
  *     edges (u < v) in CSR order; r = 3: triangles (a < b < c) by (a, b, c).
  *   - Supported (r, s): (1,2), (1,3), (2,3), (2,4), (3,4) with kernels of their own, and (1,4),
- *     (2,5), (3,5), (3,6) through the generic listing of the (s-r)-cliques of each r-clique's
- *     common neighbourhood. Others return ND_EINVAL.
+ *     (2,5), (3,5), (3,6), (4,5), (4,6) through the generic listing of the (s-r)-cliques of each
+ *     r-clique's common neighbourhood (r = 4 adds a 4-clique index: per triangle (a<b<c), the
+ *     vertices d > c adjacent to all three, ascending). Others return ND_EINVAL.
  *   - All work is issued on the context's stream; synchronous calls synchronise that stream
  *     before returning.
  */
@@ -229,7 +230,7 @@ ND_API int nd_round_times(nd_graph *g, int64_t *ns_out, int64_t cap);
 
 /* The r-cliques themselves (the inverse index map, Section 5.3): tuples_out receives n_r
  * ascending tuples of r int32 vertex ids in canonical order (host, or device with
- * ND_PTR_DEVICE; NULL to query n_r only). r in {1, 2, 3}. Errors: ND_EINVAL, ND_ENOMEM. */
+ * ND_PTR_DEVICE; NULL to query n_r only). r in {1, 2, 3, 4}. Errors: ND_EINVAL, ND_ENOMEM. */
 ND_API int nd_rcliques(nd_graph *g, int r, int32_t *tuples_out, int flags, int64_t *n_r_out);
 
 /* ---- batches and serving --------------------------------------------------------------

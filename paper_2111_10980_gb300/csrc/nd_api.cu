@@ -219,8 +219,10 @@ extern "C" int64_t nd_kernel_launches(void) { return nd_total_launches(); }
 static void free_derived(nd_graph* g) {
     nd_ctx* c = g->ctx;
     for (DBuf* b : {&g->split, &g->ebase, &g->pos2e, &g->eu, &g->ev, &g->dg_rp, &g->dg_col, &g->dg_eid, &g->et_rp,
-                    &g->et_w, &g->et_t, &g->tbase, &g->tri_e, &g->tri_pos})
+                    &g->et_w, &g->et_t, &g->tbase, &g->tri_e, &g->tri_pos, &g->qbase, &g->qval})
         nd_free(c, *b);
+    g->have_quad = false;
+    g->n4 = 0;
     g->have_base = false;
     g->edge_mindeg = -1;
     g->orient = -1;
@@ -347,6 +349,9 @@ GraphView nd_view(const nd_graph* g) {
     v.n3 = g->n3;
     v.hoff = (const int64_t*)g->hoff.p;
     v.htab = (const NdHashSlot*)g->htab.p;
+    v.qbase = (const int64_t*)g->qbase.p;
+    v.qval = (const int32_t*)g->qval.p;
+    v.n4 = g->n4;
     return v;
 }
 
@@ -500,7 +505,41 @@ static int ensure_tri(nd_graph* g) {
 }
 
 static bool rs_supported(int r, int s) {
-    return (r == 1 && s >= 2 && s <= 4) || (r == 2 && s >= 3 && s <= 5) || (r == 3 && s >= 4 && s <= 6);
+    return (r == 1 && s >= 2 && s <= 4) || (r == 2 && s >= 3 && s <= 5) || (r == 3 && s >= 4 && s <= 6) ||
+           (r == 4 && s >= 5 && s <= 6);
+}
+
+// 4-clique index (r = 4): children of every triangle (count, scan, fill)
+static int ensure_quad(nd_graph* g) {
+    if (g->have_quad) return ND_OK;
+    nd_ctx* c = g->ctx;
+    cudaStream_t st = c->stream;
+    int64_t n3 = g->n3;
+    DBuf qcnt, tmp;
+    int rc = ND_OK;
+    if ((rc = nd_alloc(c, qcnt, sizeof(int64_t) * std::max<int64_t>(n3, 1))) ||
+        (rc = nd_alloc(c, tmp, nd_scan_tmp_bytes(n3))) || (rc = nd_alloc(c, g->qbase, sizeof(int64_t) * (n3 + 1)))) {
+        nd_free(c, qcnt);
+        nd_free(c, tmp);
+        return rc;
+    }
+    GraphView v = nd_view(g);
+    nd_quad_count(v, (int64_t*)qcnt.p, st);
+    nd_scan_i64((const int64_t*)qcnt.p, (int64_t*)g->qbase.p, n3, tmp.p, st);
+    int64_t n4 = 0;
+    rc = nd_check_launch("4-clique index");
+    if (!rc) rc = read_back(g, (int64_t*)g->qbase.p + n3, &n4, "4-clique index");
+    nd_free(c, qcnt);
+    nd_free(c, tmp);
+    if (rc) return rc;
+    if (n4 > INT32_MAX) return nd_set_error(ND_EOVERFLOW, "%lld 4-cliques: more than 2^31-1", (long long)n4);
+    ND_TRY(nd_alloc(c, g->qval, sizeof(int32_t) * std::max<int64_t>(n4, 1)));
+    g->n4 = n4;
+    v = nd_view(g);
+    nd_quad_fill(v, (const int64_t*)g->qbase.p, (int32_t*)g->qval.p, st);
+    ND_TRY(nd_check_launch("4-clique index"));
+    g->have_quad = true;
+    return ND_OK;
 }
 
 static int64_t binom64(int64_t a, int b) {
@@ -523,7 +562,8 @@ int nd_prepare(nd_graph* g, int r, int s, int64_t* n_r, double* t_orient, double
     int rc = ensure_base(g);
     if (!rc && g->orient < 0) rc = build_dg(g, ND_ORIENT_DEGREE);
     cudaEventRecord(e1, c->stream);
-    if (!rc && r == 3) rc = ensure_tri(g);
+    if (!rc && r >= 3) rc = ensure_tri(g);
+    if (!rc && r == 4) rc = ensure_quad(g);
     cudaEventRecord(e2, c->stream);
     if (!rc) rc = nd_sync(c, "prepare");
     float a = 0, b = 0;
@@ -537,7 +577,7 @@ int nd_prepare(nd_graph* g, int r, int s, int64_t* n_r, double* t_orient, double
     if (rc) return rc;
     if (t_orient) *t_orient = a;
     if (t_index) *t_index = b;
-    *n_r = r == 1 ? g->n : r == 2 ? g->m : g->n3;
+    *n_r = r == 1 ? g->n : r == 2 ? g->m : r == 3 ? g->n3 : g->n4;
     return ND_OK;
 }
 
@@ -1008,7 +1048,7 @@ extern "C" int nd_decompose(nd_graph* g, int r, int s, int count_width, int32_t*
     int rc = nd_decompose_dev(g, r, s, count_width, flags, po, st);
     nd_ctx* c = g->ctx;
     if (!rc) {
-        int64_t n_r = (r == 1) ? g->n : (r == 2) ? g->m : g->n3;
+        int64_t n_r = (r == 1) ? g->n : (r == 2) ? g->m : (r == 3) ? g->n3 : g->n4;
         cudaMemcpyKind kind = (flags & ND_PTR_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
         cudaError_t e = cudaSuccess;
         if (core_out && n_r) e = cudaMemcpyAsync(core_out, po.core.p, 4 * n_r, kind, c->stream);
@@ -1052,7 +1092,7 @@ extern "C" int nd_round_times(nd_graph* g, int64_t* ns_out, int64_t cap) {
 
 extern "C" int nd_rcliques(nd_graph* g, int r, int32_t* tuples_out, int flags, int64_t* n_r_out) {
     if (!g) return nd_set_error(ND_EINVAL, "nd_rcliques: NULL graph");
-    if (r < 1 || r > 3) return nd_set_error(ND_EINVAL, "nd_rcliques: r must be 1, 2 or 3");
+    if (r < 1 || r > 4) return nd_set_error(ND_EINVAL, "nd_rcliques: r must be 1, 2, 3 or 4");
     int64_t n_r = 0;
     ND_TRY(nd_prepare(g, r, r + 1, &n_r, nullptr, nullptr));
     if (n_r_out) *n_r_out = n_r;
@@ -1065,8 +1105,10 @@ extern "C" int nd_rcliques(nd_graph* g, int r, int32_t* tuples_out, int flags, i
         nd_iota_i32((int32_t*)out.p, n_r, c->stream);
     else if (r == 2)
         nd_edge_tuples(v, (int32_t*)out.p, c->stream);
-    else
+    else if (r == 3)
         nd_tri_tuples(v, (int32_t*)out.p, c->stream);
+    else
+        nd_quad_tuples(v, (int32_t*)out.p, c->stream);
     int rc = nd_check_launch("rcliques");
     if (!rc) {
         cudaError_t e = cudaMemcpyAsync(tuples_out, out.p, sizeof(int32_t) * r * n_r,

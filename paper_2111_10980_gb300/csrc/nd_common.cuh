@@ -214,6 +214,11 @@ struct GraphView {
     // (2,3) peel with graph contraction: current length of each adjacency row (rows start at rp[v]
     // and col / pos2e point to the peel's compacted copies), else NULL
     const int32_t* rlen;
+    // 4-clique index (r = 4): per triangle t = (a<b<c) the vertices d > c adjacent to a, b and c,
+    // ascending, in qval[qbase[t] .. qbase[t+1]); a 4-clique's id is its position in qval
+    const int64_t* qbase;
+    const int32_t* qval;
+    int64_t n4;
 };
 
 // Control block of the device-resident peeling loop (one per decomposition).
@@ -369,6 +374,10 @@ void nd_edge_fill(const GraphView& g, int64_t* et_rp, int64_t* tbase, int32_t* e
                   int32_t* tri_e, int32_t* tri_pos, cudaStream_t st);
 void nd_edge_fill_tid(const GraphView& g, int32_t* et_t, int32_t* tri_pos, cudaStream_t st);
 void nd_tri_tuples(const GraphView& g, int32_t* out, cudaStream_t st);
+// 4-clique index: qcnt[t] = children of triangle t; then the children themselves
+void nd_quad_count(const GraphView& g, int64_t* qcnt, cudaStream_t st);
+void nd_quad_fill(const GraphView& g, const int64_t* qbase, int32_t* qval, cudaStream_t st);
+void nd_quad_tuples(const GraphView& g, int32_t* out, cudaStream_t st);
 void nd_edge_tuples(const GraphView& g, int32_t* out, cudaStream_t st);
 void nd_max_edge_mindeg(const GraphView& g, unsigned long long* out, cudaStream_t st);
 // hash directory of the triangle lists: slots per edge (0 for short lists), then the tables

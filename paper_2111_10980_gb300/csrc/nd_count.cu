@@ -173,14 +173,14 @@ __global__ void k_count24(GraphView g, CT* __restrict__ cnt) {
     }
 }
 
-// Any other supported (r,s) ((1,4), (2,5), (3,5), (3,6)): one warp per r-clique R counts the
+// Any other supported (r,s) ((1,4), (2,5), (3,5), (3,6), (4,5), (4,6)): one warp per r-clique R counts the
 // s-cliques containing it, listing the (s-r)-cliques of R's common neighbourhood from the entries
 // of its driving list (nd_gen.cuh); written once, no atomics.
 template <typename CT, int R_, int S_>
 __global__ void k_count_gen(GraphView g, CT* __restrict__ cnt, int64_t n_r) {
     int lane = threadIdx.x & 31;
     for (int64_t id = gwarp(); id < n_r; id += nwarps()) {
-        int32_t v[3];
+        int32_t v[4];
         gen_verts<R_>(g, id, v);
         const int32_t* list = nullptr;
         int64_t len = 0;
@@ -224,6 +224,10 @@ void nd_count_launch(const GraphView& g, int r, int s, CT* cnt, int64_t n_r, cud
         ND_K(k_count_gen<CT, 3, 5><<<blk, kThreads, 0, st>>>(g, cnt, n_r));
     } else if (r == 3 && s == 6) {
         ND_K(k_count_gen<CT, 3, 6><<<blk, kThreads, 0, st>>>(g, cnt, n_r));
+    } else if (r == 4 && s == 5) {
+        ND_K(k_count_gen<CT, 4, 5><<<blk, kThreads, 0, st>>>(g, cnt, n_r));
+    } else if (r == 4 && s == 6) {
+        ND_K(k_count_gen<CT, 4, 6><<<blk, kThreads, 0, st>>>(g, cnt, n_r));
     }
 }
 

@@ -1,5 +1,5 @@
 // Generic (r,s) listing for the counting and Update kernels of (r,s) without a dedicated kernel:
-// r <= 3 and s - r <= 3 ((1,4), (2,5), (3,5), (3,6)). Algorithm 1 restricted to one r-clique R:
+// r <= 4 and s - r <= 3 ((1,4), (2,5), (3,5), (3,6), (4,5), (4,6)). Algorithm 1 restricted to one r-clique R:
 // the candidates are the entries w of R's driving list (r = 1: N(v); r = 2: the shorter of N(u),
 // N(v); r = 3: the shortest of the triangle's three common-neighbour lists L(e)); w belongs to
 // I = the common neighbourhood of R when it is adjacent to every vertex of R. The (s-r)-cliques C
@@ -11,6 +11,19 @@
 
 #include "nd_common.cuh"
 
+// the triangle whose children in the 4-clique index hold position q (largest t with qbase[t] <= q)
+__device__ __forceinline__ int64_t gen_quad_parent(const GraphView& g, int64_t q) {
+    int64_t lo = 0, hi = g.n3;
+    while (hi - lo > 1) {
+        int64_t mid = (lo + hi) >> 1;
+        if (g.qbase[mid] <= q)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
 // vertices of r-clique `id`, ascending
 template <int R>
 __device__ __forceinline__ void gen_verts(const GraphView& g, int64_t id, int32_t* v) {
@@ -20,10 +33,12 @@ __device__ __forceinline__ void gen_verts(const GraphView& g, int64_t id, int32_
         v[0] = g.eu[id];
         v[1] = g.ev[id];
     } else {
-        int32_t e = g.tri_e[3 * id], e1 = g.tri_e[3 * id + 1];
+        int64_t t = R == 4 ? gen_quad_parent(g, id) : id;
+        int32_t e = g.tri_e[3 * t], e1 = g.tri_e[3 * t + 1];
         v[0] = g.eu[e];
         v[1] = g.ev[e];
         v[2] = g.ev[e1];
+        if (R == 4) v[3] = g.qval[id];
     }
 }
 
@@ -53,7 +68,12 @@ __device__ __forceinline__ int64_t gen_id(const GraphView& g, const int32_t* t) 
     if (R == 2) return e;
     int64_t lo = g.et_rp[e];
     int64_t i = nd_find(g.et_w + lo, g.et_rp[e + 1] - lo, t[2]);
-    return i < 0 ? -1 : (int64_t)g.et_t[lo + i];
+    if (i < 0) return -1;
+    int64_t tri = g.et_t[lo + i];
+    if (R == 3) return tri;
+    int64_t qb = g.qbase[tri];
+    int64_t j = nd_find(g.qval + qb, g.qbase[tri + 1] - qb, t[3]);
+    return j < 0 ? -1 : qb + j;
 }
 
 // the driving list of r-clique v (its candidates w)
@@ -69,9 +89,11 @@ __device__ __forceinline__ void gen_drive(const GraphView& g, int64_t id, const 
         list = g.col + g.rp[x];
         len = du <= dv ? du : dv;
     } else {
+        // r = 3: the triangle's own lists; r = 4: the lists of its first three vertices' triangle
+        int64_t t = R == 4 ? gen_quad_parent(g, id) : id;
         len = -1;
         for (int k = 0; k < 3; ++k) {
-            int32_t e = g.tri_e[3 * id + k];
+            int32_t e = g.tri_e[3 * t + k];
             int64_t n = g.et_rp[e + 1] - g.et_rp[e];
             if (len < 0 || n < len) {
                 len = n;
@@ -146,7 +168,7 @@ __device__ __forceinline__ bool gen_others(const GraphView& g, const int32_t* v,
     int n = 0;
     for (unsigned mask = 0; mask < (1u << S); ++mask) {
         if (__popc(mask) != R) continue;
-        int32_t t[3];
+        int32_t t[4];
         int q = 0;
         bool same = true;
 #pragma unroll

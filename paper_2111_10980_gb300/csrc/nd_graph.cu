@@ -270,6 +270,65 @@ __global__ void k_tri_tuples(GraphView g, int32_t* __restrict__ out) {
     }
 }
 
+// 4-clique index (the paper's T one level deeper, Section 5.1): the children of triangle
+// t = (a<b<c) are the vertices d > c adjacent to a, b and c, ascending. Any two of the triangle's
+// edge lists intersect to its common neighbourhood (L(ab) ∩ L(bc) = N(a) ∩ N(b) ∩ N(c)), so a
+// warp walks the part above c of the shortest list and searches the second shortest; matches are
+// compacted in order with a ballot (count pass, then fill pass at qbase[t]).
+template <bool kFill>
+__device__ __forceinline__ int64_t quad_children(const GraphView& g, int64_t t, int32_t* out) {
+    int lane = threadIdx.x & 31;
+    int32_t e[3] = {g.tri_e[3 * t], g.tri_e[3 * t + 1], g.tri_e[3 * t + 2]};
+    int32_t c = g.ev[e[1]];  // edges (ab, ac, bc): the largest vertex is ac's upper end
+    int64_t b[3], n[3];
+    for (int k = 0; k < 3; ++k) {
+        b[k] = g.et_rp[e[k]];
+        n[k] = g.et_rp[e[k] + 1] - b[k];
+    }
+    int i0 = 0, i1 = 1;
+    if (n[1] < n[0]) i0 = 1, i1 = 0;
+    if (n[2] < n[i0]) i1 = i0, i0 = 2;
+    else if (n[2] < n[i1]) i1 = 2;
+    const int32_t* xs = g.et_w + b[i0];
+    const int32_t* ys = g.et_w + b[i1];
+    int64_t xlo = nd_lower_bound(xs, n[i0], c + 1), ylo = nd_lower_bound(ys, n[i1], c + 1);
+    int64_t pos = 0;
+    for (int64_t p0 = xlo; p0 < n[i0]; p0 += 32) {
+        int64_t p = p0 + lane;
+        bool hit = p < n[i0] && nd_find(ys + ylo, n[i1] - ylo, xs[p]) >= 0;
+        unsigned m = __ballot_sync(0xffffffffu, hit);
+        if (kFill && hit) out[pos + __popc(m & nd_lanemask_lt())] = xs[p];
+        pos += __popc(m);
+    }
+    return pos;
+}
+
+__global__ void k_quad_count(GraphView g, int64_t* __restrict__ qcnt) {
+    for (int64_t t = gwarp(); t < g.n3; t += nwarps()) {
+        int64_t k = quad_children<false>(g, t, nullptr);
+        if ((threadIdx.x & 31) == 0) qcnt[t] = k;
+    }
+}
+
+__global__ void k_quad_fill(GraphView g, const int64_t* __restrict__ qbase, int32_t* __restrict__ qval) {
+    for (int64_t t = gwarp(); t < g.n3; t += nwarps()) quad_children<true>(g, t, qval + qbase[t]);
+}
+
+// the inverse map of the 4-clique index: 4-clique q -> (a, b, c, d), one warp per triangle
+__global__ void k_quad_tuples(GraphView g, int32_t* __restrict__ out) {
+    int lane = threadIdx.x & 31;
+    for (int64_t t = gwarp(); t < g.n3; t += nwarps()) {
+        int32_t e = g.tri_e[3 * t], e1 = g.tri_e[3 * t + 1];
+        int32_t a = g.eu[e], b = g.ev[e], c = g.ev[e1];
+        for (int64_t q = g.qbase[t] + lane; q < g.qbase[t + 1]; q += 32) {
+            out[4 * q] = a;
+            out[4 * q + 1] = b;
+            out[4 * q + 2] = c;
+            out[4 * q + 3] = g.qval[q];
+        }
+    }
+}
+
 __global__ void k_edge_tuples(GraphView g, int32_t* __restrict__ out) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < g.m; e += (int64_t)gridDim.x * blockDim.x) {
         out[2 * e] = g.eu[e];
@@ -402,4 +461,19 @@ void nd_tri_tuples(const GraphView& g, int32_t* out, cudaStream_t st) {
 void nd_edge_tuples(const GraphView& g, int32_t* out, cudaStream_t st) {
     if (g.m <= 0) return;
     ND_K(k_edge_tuples<<<blocks_for_threads(g.m), kThreads, 0, st>>>(g, out));
+}
+
+void nd_quad_count(const GraphView& g, int64_t* qcnt, cudaStream_t st) {
+    if (g.n3 <= 0) return;
+    ND_K(k_quad_count<<<blocks_for_warps(g.n3), kThreads, 0, st>>>(g, qcnt));
+}
+
+void nd_quad_fill(const GraphView& g, const int64_t* qbase, int32_t* qval, cudaStream_t st) {
+    if (g.n3 <= 0) return;
+    ND_K(k_quad_fill<<<blocks_for_warps(g.n3), kThreads, 0, st>>>(g, qbase, qval));
+}
+
+void nd_quad_tuples(const GraphView& g, int32_t* out, cudaStream_t st) {
+    if (g.n3 <= 0) return;
+    ND_K(k_quad_tuples<<<blocks_for_warps(g.n3), kThreads, 0, st>>>(g, out));
 }

@@ -57,6 +57,10 @@ struct nd_graph {
     // triangle index
     bool have_tri = false;
     int64_t n3 = 0;
+    // 4-clique index
+    bool have_quad = false;
+    int64_t n4 = 0;
+    DBuf qbase, qval;
     DBuf et_rp, et_w, et_t, tbase, tri_e, tri_pos;
     // hash directory of the long triangle lists, held only while a (3,4) decomposition runs
     DBuf hoff, htab, hpos;

@@ -705,7 +705,7 @@ struct Prep {
     int64_t b[3];
     int64_t n[3];
     int64_t h[3];  // (3,4): hash-table offset of the list, -1 when it is searched by bisection
-    int32_t v[3];  // generic (r,s): the vertices of R
+    int32_t v[4];  // generic (r,s): the vertices of R
     const int32_t* lp;  // generic (r,s): the driving list
 };
 
@@ -1124,7 +1124,7 @@ struct Upd34 {
     }
 };
 
-// Any other (r,s) with r <= 3 and s - r <= 3 ((1,4), (2,5), (3,5), (3,6)): the candidates are
+// Any other (r,s) with r <= 4 and s - r <= 3 ((1,4), (2,5), (3,5), (3,6), (4,5), (4,6)): the candidates are
 // the entries of R's driving list; each lists the (s-r)-cliques of R's common neighbourhood that
 // start at it (nd_gen.cuh), looks up the ids of the other r-subsets of every S = R + C and applies
 // Update-Func. A lookup that fails means an inconsistent index (ctl->err bit 16).
@@ -1671,6 +1671,12 @@ void nd_peel_update(const GraphView& g, int r, int s, const PeelView<CT>& P, cud
     } else if (r == 3 && s == 6) {
         ND_K(k_update<CT, UpdGen<CT, 3, 6>><<<nb, kThreads, 0, st>>>(g, P));
         ND_K(k_update_heavy<CT, UpdGen<CT, 3, 6>><<<nb, kThreads, 0, st>>>(g, P));
+    } else if (r == 4 && s == 5) {
+        ND_K(k_update<CT, UpdGen<CT, 4, 5>><<<nb, kThreads, 0, st>>>(g, P));
+        ND_K(k_update_heavy<CT, UpdGen<CT, 4, 5>><<<nb, kThreads, 0, st>>>(g, P));
+    } else if (r == 4 && s == 6) {
+        ND_K(k_update<CT, UpdGen<CT, 4, 6>><<<nb, kThreads, 0, st>>>(g, P));
+        ND_K(k_update_heavy<CT, UpdGen<CT, 4, 6>><<<nb, kThreads, 0, st>>>(g, P));
     }
 }
 
@@ -1786,6 +1792,8 @@ cudaError_t nd_peel_persistent(const GraphView& g, int r, int s, const PeelView<
     if (r == 2 && s == 5) return launch_peel_loop<CT, UpdGen<CT, 2, 5>, false>(g, P, st);
     if (r == 3 && s == 5) return launch_peel_loop<CT, UpdGen<CT, 3, 5>, false>(g, P, st);
     if (r == 3 && s == 6) return launch_peel_loop<CT, UpdGen<CT, 3, 6>, false>(g, P, st);
+    if (r == 4 && s == 5) return launch_peel_loop<CT, UpdGen<CT, 4, 5>, false>(g, P, st);
+    if (r == 4 && s == 6) return launch_peel_loop<CT, UpdGen<CT, 4, 6>, false>(g, P, st);
     return cudaErrorInvalidValue;
 }
 

@@ -34,16 +34,19 @@
 namespace {
 
 bool rs_ok(int r, int s) {
-    return (r == 1 && s >= 2 && s <= 4) || (r == 2 && s >= 3 && s <= 5) || (r == 3 && s >= 4 && s <= 6);
+    return (r == 1 && s >= 2 && s <= 4) || (r == 2 && s >= 3 && s <= 5) || (r == 3 && s >= 4 && s <= 6) ||
+           (r == 4 && s >= 5 && s <= 6);
 }
 
 __global__ void k_gather_offsets(const int64_t* __restrict__ ebase, const int64_t* __restrict__ tbase,
-                                 const int64_t* __restrict__ voff, int64_t count, int r, int64_t* __restrict__ out) {
+                                 const int64_t* __restrict__ qbase, const int64_t* __restrict__ voff, int64_t count,
+                                 int r, int64_t* __restrict__ out) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= count; i += (int64_t)gridDim.x * blockDim.x) {
         int64_t v = voff[i];
         int64_t o = v;
         if (r >= 2) o = ebase[v];
         if (r >= 3) o = tbase[o];
+        if (r >= 4) o = qbase[o];
         out[i] = o;
     }
 }
@@ -240,10 +243,11 @@ int run_group(nd_ctx* ctx, nd_request* const* reqs, std::vector<int> idx, nd_bat
         std::vector<int64_t> off(K + 1);
         if (!rc) {
             // canonical offset of each request's first r-clique: r = 1 its first vertex, r = 2 the
-            // edge base there, r = 3 the triangle base at that edge
+            // edge base there, r = 3 the triangle base at that edge, r = 4 the 4-clique base at that
+            // triangle
             GraphView v = nd_view(g);
             ND_K(k_gather_offsets<<<std::max<int64_t>(1, (K + 1 + 255) / 256), 256, 0, stream>>>(
-                v.ebase, v.tbase, (const int64_t*)doffs.p, K, r, (int64_t*)doffs.p + (K + 1)));
+                v.ebase, v.tbase, v.qbase, (const int64_t*)doffs.p, K, r, (int64_t*)doffs.p + (K + 1)));
             rc = nd_check_launch("batch offsets");
             if (!rc) {
                 cudaMemcpyAsync(off.data(), (int64_t*)doffs.p + (K + 1), sizeof(int64_t) * (K + 1),

@@ -192,9 +192,10 @@ def test_errors_are_reported(nd, ctx):
     with pytest.raises(nd.NdError):
         nd.nd_load_csr(ctx, asym.rowptr, col, flags=nd.ND_VALIDATE)
     G = nd.nd_load_csr(ctx, g.rowptr, g.col)
-    with pytest.raises(nd.NdError) as ei:
-        nd.nd_decompose(G, 4, 5)
-    assert ei.value.code == nd.ND_EINVAL
+    for r, s in [(4, 7), (2, 6), (5, 6)]:
+        with pytest.raises(nd.NdError) as ei:
+            nd.nd_decompose(G, r, s)
+        assert ei.value.code == nd.ND_EINVAL
     nd.nd_graph_free(G)
     small = nd.nd_ctx_create(0, mem_budget=1 << 12)
     with pytest.raises(nd.NdError) as ei:
