@@ -7,10 +7,11 @@
 //     list and binary-searches the others; the result is written once, with no atomics.
 //     For r = 3 the lists are the per-edge common-neighbour tables L(e) of the triangle index
 //     (|L(e)| is the edge's triangle support, far shorter than the vertex degrees).
-//   * s = r + 2  ((1,3), (2,4)): one warp per vertex u lists the s-cliques whose lowest vertex
-//     in the orientation is u (Algorithm 1 over DG: I' = I ∩ N_DG(v) at each level) and adds 1
-//     to each of their C(s,r) r-subsets (Count-Func), with one aggregated atomic for the
-//     r-subsets shared by a whole level.
+//   * s = r + 2  ((1,3), (2,4)): the s-cliques are listed once each over DG (Algorithm 1:
+//     I' = I ∩ N_DG(v) at each level) and add 1 to each of their C(s,r) r-subsets (Count-Func),
+//     with one aggregated atomic for an r-subset shared by a whole level: (1,3) one warp per
+//     lowest vertex; (2,4) one warp per lowest DG edge, the pairs of its last level spread over the
+//     lanes.
 #include "nd_common.cuh"
 #include "nd_gen.cuh"
 
@@ -132,44 +133,127 @@ __global__ void k_count13(GraphView g, CT* __restrict__ cnt) {
     }
 }
 
-// (2,4): every 4-clique (u, v, w, x) of DG adds 1 to its six edges.
+// (2,4), one warp per DG edge u -> v: the 4-cliques whose two lowest vertices (in the orientation)
+// are u and v are u, v plus a DG edge w -> x inside I = N_DG(u) ∩ N_DG(v). The warp stages I in
+// shared memory (ascending ids, with the edge ids u-w and v-w and the out-list bounds of each w),
+// numbers the candidate pairs (w, k-th out-neighbour of w) through a prefix sum of the out-degrees
+// and spreads them evenly over its lanes; a lane finds x in the staged I by bisection and adds 1 to
+// the 4-clique's edges w-x, u-x, v-x, u-w, v-w; u-v gets the warp's total once. An edge whose I does
+// not fit the stage (more than kC24 vertices) is listed by the lanes walking out-lists instead.
+constexpr int kC24 = 128;
+
+__device__ __forceinline__ int stage_find24(const int32_t* a, int n, int32_t x) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (a[mid] < x)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return (lo < n && a[lo] == x) ? lo : -1;
+}
+
 template <typename CT>
-__global__ void k_count24(GraphView g, CT* __restrict__ cnt) {
-    int lane = threadIdx.x & 31;
-    for (int64_t u = gwarp(); u < g.n; u += nwarps()) {
-        int64_t ub = g.dg_rp[u], ue = g.dg_rp[u + 1];
-        for (int64_t jv = ub; jv < ue; ++jv) {
-            int32_t v = g.dg_col[jv];
-            int32_t e_uv = g.dg_eid[jv];
-            int64_t vb = g.dg_rp[v], vn = g.dg_rp[v + 1] - vb;
-            int c_uv = 0;
-            for (int64_t i = ub + lane; i < ue; i += 32) {
-                int32_t w = g.dg_col[i];
+__global__ void __launch_bounds__(kThreads) k_count24_flat(GraphView g, CT* __restrict__ cnt) {
+    __shared__ int32_t s_w[kWarpsPerBlock][kC24], s_eu[kWarpsPerBlock][kC24], s_ev[kWarpsPerBlock][kC24],
+        s_b[kWarpsPerBlock][kC24], s_p[kWarpsPerBlock][kC24 + 1];
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int32_t *sw = s_w[wid], *seu = s_eu[wid], *sev = s_ev[wid], *sb = s_b[wid], *sp = s_p[wid];
+    for (int64_t j = gwarp(); j < g.m; j += nwarps()) {
+        // u: the vertex whose out-list holds DG position j
+        int64_t lo = 0, hi = g.n;
+        while (hi - lo > 1) {
+            int64_t mid = (lo + hi) >> 1;
+            if (g.dg_rp[mid] <= j)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        const int32_t u = (int32_t)lo, v = g.dg_col[j], e_uv = g.dg_eid[j];
+        const int64_t ub = g.dg_rp[u], ue = g.dg_rp[u + 1], vb = g.dg_rp[v], vn = g.dg_rp[v + 1] - vb;
+        // stage I = N_DG(u) ∩ N_DG(v) in order
+        int c = 0;
+        for (int64_t p0 = ub; p0 < ue; p0 += 32) {
+            int64_t p = p0 + lane;
+            int64_t q = p < ue ? nd_find(g.dg_col + vb, vn, g.dg_col[p]) : -1;
+            unsigned mk = __ballot_sync(full, q >= 0);
+            if (q >= 0) {
+                int at = c + __popc(mk & nd_lanemask_lt());
+                if (at < kC24) {
+                    int32_t w = g.dg_col[p];
+                    sw[at] = w;
+                    seu[at] = g.dg_eid[p];
+                    sev[at] = g.dg_eid[vb + q];
+                    sb[at] = (int32_t)g.dg_rp[w];
+                    sp[at] = (int32_t)(g.dg_rp[w + 1] - g.dg_rp[w]);
+                }
+            }
+            c += __popc(mk);
+        }
+        __syncwarp();
+        unsigned long long c_uv = 0;
+        if (c <= kC24) {
+            // exclusive prefix of the out-degrees (c <= kC24: at most four 32-wide chunks)
+            int32_t carry = 0;
+            for (int c0 = 0; c0 < c; c0 += 32) {
+                int i = c0 + lane;
+                int32_t d = i < c ? sp[i] : 0, inc = d;
+                for (int o = 1; o < 32; o <<= 1) {
+                    int32_t y = __shfl_up_sync(full, inc, o);
+                    if (lane >= o) inc += y;
+                }
+                if (i < c) sp[i] = carry + inc - d;
+                carry += __shfl_sync(full, inc, 31);
+            }
+            if (lane == 0) sp[c] = carry;
+            __syncwarp();
+            for (int32_t p = lane; p < carry; p += 32) {
+                int a = 0, b = c;  // owner: the last i with sp[i] <= p
+                while (b - a > 1) {
+                    int mid = (a + b) >> 1;
+                    if (sp[mid] <= p)
+                        a = mid;
+                    else
+                        b = mid;
+                }
+                int64_t jx = (int64_t)sb[a] + (p - sp[a]);
+                int k = stage_find24(sw, c, g.dg_col[jx]);
+                if (k < 0) continue;
+                ++c_uv;
+                nd_atomic_add(&cnt[g.dg_eid[jx]], 1);
+                nd_atomic_add(&cnt[seu[k]], 1);
+                nd_atomic_add(&cnt[sev[k]], 1);
+                nd_atomic_add(&cnt[seu[a]], 1);
+                nd_atomic_add(&cnt[sev[a]], 1);
+            }
+        } else {
+            // I does not fit the stage: the lanes take the w of N_DG(u) ∩ N_DG(v) and walk their
+            // out-lists, searching x in both lists
+            for (int64_t p = ub + lane; p < ue; p += 32) {
+                int32_t w = g.dg_col[p];
                 int64_t q = nd_find(g.dg_col + vb, vn, w);
                 if (q < 0) continue;
-                int32_t e_uw = g.dg_eid[i], e_vw = g.dg_eid[vb + q];
-                int64_t wb = g.dg_rp[w], we = g.dg_rp[w + 1];
-                int c_w = 0;
-                for (int64_t jx = wb; jx < we; ++jx) {
+                int32_t e_uw = g.dg_eid[p], e_vw = g.dg_eid[vb + q];
+                for (int64_t jx = g.dg_rp[w]; jx < g.dg_rp[w + 1]; ++jx) {
                     int32_t x = g.dg_col[jx];
                     int64_t pux = nd_find(g.dg_col + ub, ue - ub, x);
                     if (pux < 0) continue;
                     int64_t pvx = nd_find(g.dg_col + vb, vn, x);
                     if (pvx < 0) continue;
-                    c_w++;
+                    ++c_uv;
+                    nd_atomic_add(&cnt[g.dg_eid[jx]], 1);
                     nd_atomic_add(&cnt[g.dg_eid[ub + pux]], 1);
                     nd_atomic_add(&cnt[g.dg_eid[vb + pvx]], 1);
-                    nd_atomic_add(&cnt[g.dg_eid[jx]], 1);
-                }
-                if (c_w) {
-                    nd_atomic_add(&cnt[e_uw], c_w);
-                    nd_atomic_add(&cnt[e_vw], c_w);
-                    c_uv += c_w;
+                    nd_atomic_add(&cnt[e_uw], 1);
+                    nd_atomic_add(&cnt[e_vw], 1);
                 }
             }
-            c_uv = warp_sum(c_uv);
-            if (lane == 0 && c_uv) nd_atomic_add(&cnt[e_uv], c_uv);
         }
+        for (int o = 16; o > 0; o >>= 1) c_uv += __shfl_down_sync(full, c_uv, o);
+        if (lane == 0 && c_uv) nd_atomic_add(&cnt[e_uv], (int64_t)c_uv);
+        __syncwarp();
     }
 }
 
@@ -215,7 +299,7 @@ void nd_count_launch(const GraphView& g, int r, int s, CT* cnt, int64_t n_r, cud
         ND_K(k_count13<CT><<<blocks_for_warps(g.n), kThreads, 0, st>>>(g, cnt));
     } else if (r == 2 && s == 4) {
         ND_K(k_zero<CT><<<blk, kThreads, 0, st>>>(cnt, n_r));
-        ND_K(k_count24<CT><<<blocks_for_warps(g.n), kThreads, 0, st>>>(g, cnt));
+        ND_K(k_count24_flat<CT><<<blocks_for_warps(g.m), kThreads, 0, st>>>(g, cnt));
     } else if (r == 1 && s == 4) {
         ND_K(k_count_gen<CT, 1, 4><<<blk, kThreads, 0, st>>>(g, cnt, n_r));
     } else if (r == 2 && s == 5) {
