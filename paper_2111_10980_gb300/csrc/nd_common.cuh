@@ -16,6 +16,11 @@
 //                        tri_pos int32[3 n3] offset of the triangle's entry in L(ab), L(ac), L(bc)
 //   During a (3,4) peel, et_rnd int32[3 n3] (beside et_t) holds, per entry, the round in which
 //   the entry's triangle is peeled (INT32_MAX while unscheduled).
+//   4-clique index       qbase int64[n3+1], qval int32[n4]: per triangle (a<b<c) the vertices d > c
+//     (r = 4)            adjacent to a, b and c, ascending; a 4-clique's id is its position in qval
+//   Peel state (per decomposition): counts, rounds, cores, the A / N / L work lists, the control
+//   block PeelCtl, and when enabled the (2,3) contraction's row copies, the dense bucket array,
+//   the (2,4) heavy-phase scratch slices.
 #pragma once
 
 #include <cuda_runtime.h>

@@ -31,6 +31,15 @@
 //     warp applies S's effect, subtracting exactly 1 from every r-subset not in A. The paper
 //     has each of the a members of A subtract 1/a; the owner rule gives the same total (1 per
 //     live S and surviving member) with integer atomics and without double counting.
+// Warps take A in dynamic chunks; r-cliques with long driving lists go to a heavy phase that
+// gives each a block ((2,4) in the persistent kernel: stage per block, then the pairs of all
+// heavy edges over the whole grid).
+//
+// Also here: the (2,3) graph contraction of Section 5.6 (rows that lost a quarter of their entries
+// are compacted once 2n edges were peeled since the previous contraction), the dense buckets with
+// the doubling search of Section 4.2 (Discussion) as an alternative way to find the next level,
+// and the three launch modes of the loop: one cooperative persistent kernel (default), one CUDA
+// graph with WHILE / IF nodes, or every phase launched.
 #include "nd_common.cuh"
 #include "nd_gen.cuh"
 
