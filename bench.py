@@ -87,8 +87,8 @@ WORKLOADS = {
 
 # The density sweep of Fig. 13: R-MAT with a=0.5, b=c=0.1 (d=0.3), duplicate edges removed, at
 # several edge factors, for (2,3), (3,4) and (4,5).
-SWEEP_SCALE = 15
-SWEEP_EDGE_FACTORS = [4, 8, 16, 32]
+SWEEP_SCALE = 17
+SWEEP_EDGE_FACTORS = [8, 16, 32, 64]
 SWEEP_RS = [(2, 3), (3, 4), (4, 5)]
 
 
