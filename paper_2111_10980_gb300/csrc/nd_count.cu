@@ -90,10 +90,14 @@ __global__ void k_count34(GraphView g, CT* __restrict__ cnt) {
             b0 = b2, n0 = n2, e0 = e2, b2 = tb, n2 = tn, e2 = te;
         }
         if (n2 < n1) b1 = b2, n1 = n2, e1 = e2;
+        // the longer list is probed in the hash directory once it is more than about twice the
+        // shorter (measured on R-MAT scale 20: the merge pays only below that); without a table, the
+        // warp merge up to 8x and bisection beyond
         int c = 0;
-        if (nd_prefer_merge(n0, n1)) {
+        const bool probe = g.htab && nd_hashed(n1) && n1 > 2 * n0 + 64;
+        if (!probe && nd_prefer_merge(n0, n1)) {
             nd_warp_merge(g.et_w + b0, n0, g.et_w + b1, n1, [&](bool f, int64_t, int64_t) { c += f ? 1 : 0; });
-        } else if (g.htab && nd_hashed(n1)) {
+        } else if (probe) {
             // the long list has a hash directory: one probe instead of a bisection
             const NdHashSlot* tab = g.htab + g.hoff[e1];
             int k = nd_hash_bits(n1);
