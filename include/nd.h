@@ -67,9 +67,10 @@ extern "C" {
 #define ND_PEEL_LOOP_GRAPH 0x8  /* nd_decompose: run the peeling loop as one CUDA graph (WHILE/IF nodes) */
 #define ND_PEEL_PERSISTENT 0x10 /* nd_decompose: run the peeling loop as one cooperative kernel (default
                                    when none of these three flags is given and the launch is possible) */
-#define ND_CONTRACT_OFF 0x20    /* nd_decompose (2,3): no graph contraction (Section 5.6) */
-#define ND_CONTRACT_ALWAYS 0x40 /* nd_decompose (2,3): contract before every round, every row that lost an
-                                   entry (exercises the contraction; slower than the default) */
+#define ND_CONTRACT_OFF 0x20    /* nd_decompose (2,3): no graph contraction (Section 5.6); (3,4): no
+                                   contraction of the triangle lists (entries of peeled triangles stay) */
+#define ND_CONTRACT_ALWAYS 0x40 /* nd_decompose (2,3), (3,4): contract before every round, every row or list
+                                   that lost an entry (exercises the contraction; slower than the default) */
 #define ND_DENSE_BUCKETS 0x80   /* nd_decompose: find each new level with the dense bucket array and its
                                    doubling search (Section 4.2 Discussion) instead of a scan of the
                                    bucket window; pays off when the range of counts is small */
@@ -111,9 +112,10 @@ typedef struct nd_stats {
                             bucket window), [1] window refill, [2] selection of A, [3] id-order
                             rebuild of A, [4] Update, [5] Update of the heavy r-cliques */
     double t_contract_ms;/* persistent peel kernel only: wall time of the graph contractions (block 0) */
-    int64_t contractions;/* graph contractions run ((2,3), Section 5.6): by default one whenever at least
-                            2n edges were peeled since the previous one, compacting the adjacency rows
-                            that lost at least a quarter of their entries since then */
+    int64_t contractions;/* contractions run: (2,3) graph contraction (Section 5.6), by default one
+                            whenever at least 2n edges were peeled since the previous one, compacting
+                            the adjacency rows that lost at least a quarter of their entries since
+                            then; (3,4) the same for the triangle lists, once 2m triangles were peeled */
 } nd_stats;
 
 /* ---- context ------------------------------------------------------------------------- */

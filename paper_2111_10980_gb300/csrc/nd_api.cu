@@ -726,6 +726,8 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
     }
     // (2,3) graph contraction (Section 5.6): compacted copies of the rows and their lengths
     bool contract = r == 2 && s == 3 && !(flags & ND_CONTRACT_OFF);
+    // (3,4): the same for the triangle lists (compacted copies of the lists and entry offsets)
+    bool contract34 = r == 3 && s == 4 && !(flags & ND_CONTRACT_OFF);
     // dense buckets (Section 4.2 Discussion): one bucket per count value up to the largest count
     bool dense = flags & ND_DENSE_BUCKETS;
     int64_t bmax = 0;
@@ -740,7 +742,9 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
         ND_TRY(read_back(g, g->scal.p, &mx, "peel setup"));
         bmax = (int64_t)mx + 1;
     }
-    DBuf ctl, A0, A1, N0, N1, L0, L1, H, rs, rl, rt, etr, hsc, abits, ccol, cpos, clen, cprev, bcnt, hcnt, hpre;
+    DBuf ctl, A0, A1, N0, N1, L0, L1, H, rs, rl, rt, etr, hsc, abits, ccol, cpos, clen, cprev, bcnt, hcnt, hpre, lw, lt,
+        ltp, llen, lprev;
+    const int64_t nent = std::max<int64_t>(3 * g->n3, 1);
     if ((rc = nd_alloc(c, ctl, sizeof(PeelCtl))) || (rc = nd_alloc(c, A0, 4 * cap)) || (rc = nd_alloc(c, A1, 4 * cap)) ||
         (rc = nd_alloc(c, N0, 4 * cap)) || (rc = nd_alloc(c, N1, 4 * cap)) || (rc = nd_alloc(c, L0, 4 * cap)) ||
         (rc = nd_alloc(c, L1, 4 * cap)) || (rc = nd_alloc(c, H, 4 * hcap)) || (rc = nd_alloc(c, rs, 8 * rcap)) ||
@@ -752,9 +756,12 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
                       (rc = nd_alloc(c, clen, 4 * std::max<int64_t>(g->n, 1))) ||
                       (rc = nd_alloc(c, cprev, 4 * std::max<int64_t>(g->n, 1))))) ||
         (dense && (rc = nd_alloc(c, bcnt, 4 * std::max<int64_t>(bmax, 1)))) ||
-        (staged && ((rc = nd_alloc(c, hcnt, 4 * (hslices + 1))) || (rc = nd_alloc(c, hpre, 8 * (hslices + 1)))))) {
+        (staged && ((rc = nd_alloc(c, hcnt, 4 * (hslices + 1))) || (rc = nd_alloc(c, hpre, 8 * (hslices + 1))))) ||
+        (contract34 && ((rc = nd_alloc(c, lw, 4 * nent)) || (rc = nd_alloc(c, lt, 4 * nent)) ||
+                        (rc = nd_alloc(c, ltp, 4 * nent)) || (rc = nd_alloc(c, llen, 4 * std::max<int64_t>(g->m, 1))) ||
+                        (rc = nd_alloc(c, lprev, 4 * std::max<int64_t>(g->m, 1)))))) {
         for (DBuf* b : {&ctl, &A0, &A1, &N0, &N1, &L0, &L1, &H, &rs, &rl, &rt, &etr, &hsc, &abits, &ccol, &cpos, &clen,
-                        &cprev, &bcnt, &hcnt, &hpre})
+                        &cprev, &bcnt, &hcnt, &hpre, &lw, &lt, &ltp, &llen, &lprev})
             nd_free(c, *b);
         return rc;
     }
@@ -840,6 +847,30 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
         v.rlen = P.clen;
         bool always = flags & ND_CONTRACT_ALWAYS;
         contract_every = always ? 1 : std::max<int64_t>(2 * (int64_t)g->n, 1);
+        contract_shift = always ? 0 : 2;
+    }
+    P.lw = P.lt = P.ltp = P.llen = P.lprev = nullptr;
+    if (contract34) {
+        // lists that lost a quarter of their entries, once 2m triangles (two per list) were peeled
+        // since the previous contraction; ND_CONTRACT_ALWAYS: before every round, every list that
+        // lost an entry
+        P.lw = (int32_t*)lw.p;
+        P.lt = (int32_t*)lt.p;
+        P.ltp = (int32_t*)ltp.p;
+        P.llen = (int32_t*)llen.p;
+        P.lprev = (int32_t*)lprev.p;
+        if (g->n3) {
+            cudaMemcpyAsync(P.lw, g->et_w.p, 4 * 3 * g->n3, cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync(P.lt, g->et_t.p, 4 * 3 * g->n3, cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync(P.ltp, g->tri_pos.p, 4 * 3 * g->n3, cudaMemcpyDeviceToDevice, st);
+        }
+        nd_row_len((const int64_t*)g->et_rp.p, (int32_t)g->m, P.llen, P.lprev, st);
+        v.et_w = P.lw;
+        v.et_t = P.lt;
+        v.llen = P.llen;
+        P.tri_pos = P.ltp;
+        bool always = flags & ND_CONTRACT_ALWAYS;
+        contract_every = always ? 1 : std::max<int64_t>(2 * g->m, 1);
         contract_shift = always ? 0 : 2;
     }
     nd_peel_init(P.ctl, n_r, max_rounds, st, (uint64_t)c->barrier_ns, (c->limit_flags & ND_LIMIT_DROP_BLOCK) ? 1 : 0,
@@ -965,7 +996,7 @@ static int run_peel(nd_graph* g, int r, int s, DBuf& cnt, int64_t n_r, int flags
         }
     }
     for (DBuf* b : {&ctl, &A0, &A1, &N0, &N1, &L0, &L1, &H, &rs, &rl, &rt, &etr, &hsc, &abits, &ccol, &cpos, &clen,
-                    &cprev, &bcnt, &hcnt, &hpre})
+                    &cprev, &bcnt, &hcnt, &hpre, &lw, &lt, &ltp, &llen, &lprev})
         nd_free(c, *b);
     return rc;
 }

@@ -219,6 +219,9 @@ struct GraphView {
     // (2,3) peel with graph contraction: current length of each adjacency row (rows start at rp[v]
     // and col / pos2e point to the peel's compacted copies), else NULL
     const int32_t* rlen;
+    // (3,4) peel with list contraction: current length of each triangle list L(e) (the lists start
+    // at et_rp[e]; et_w / et_t point to the peel's compacted copies), else NULL
+    const int32_t* llen;
     // 4-clique index (r = 4): per triangle t = (a<b<c) the vertices d > c adjacent to a, b and c,
     // ascending, in qval[qbase[t] .. qbase[t+1]); a 4-clique's id is its position in qval
     const int64_t* qbase;
@@ -333,6 +336,14 @@ struct PeelView {
     // count is c, for c < bmax (the largest initial count + 1); NULL when off
     unsigned int* bcnt;
     int64_t bmax;
+    // (3,4) list contraction: compacted copies of the triangle lists (vertex, triangle id), of the
+    // entry offsets of every triangle (tri_pos), the lists' current lengths and their lengths at the
+    // previous contraction; NULL when off (et_rnd is compacted along with them)
+    int32_t* lw;
+    int32_t* lt;
+    int32_t* ltp;
+    int32_t* llen;
+    int32_t* lprev;
     // driving-list length above which Update defers an r-clique to the heavy phase (0: the
     // variant's built-in threshold)
     int64_t heavy_work;

@@ -514,6 +514,62 @@ __device__ void phase_contract(const GraphView& g, const PeelView<CT>& P) {
 template <typename CT>
 __global__ void k_contract(GraphView g, PeelView<CT> P) { phase_contract(g, P); }
 
+// The same for the (3,4) triangle lists L(e): an entry is lost when its triangle was peeled in an
+// earlier round (its tag); a list that lost at least len_prev >> contract_shift entries since the
+// previous contraction is filtered in place, one warp per edge, moving each kept entry's vertex,
+// triangle id and tag together and recording its new offset in the triangle's entry table (the
+// slot of the entry among its triangle's three lists follows from the vertex order: for the edge
+// (a, c) and entry w, the triangle's edges are (xy, xz, yz) for x < y < z and e is xy when w > c, xz
+// when a < w < c, yz when w < a). The hash tables keep every entry: a lookup of a removed entry
+// finds its earlier tag, so the candidate is dropped as before.
+template <typename CT>
+__device__ void phase_contract34(const GraphView& g, const PeelView<CT>& P) {
+    PeelCtl* c = P.ctl;
+    if (c->done || !c->contract) return;
+    const int32_t t = c->t, shift = c->contract_shift;
+    const int lane = threadIdx.x & 31;
+    for (int64_t e = gwarp(); e < g.m; e += nwarps()) {
+        const int64_t b = g.et_rp[e];
+        const int32_t len = P.llen[e], prev = P.lprev[e];
+        int32_t alive = 0;
+        for (int32_t i = lane; i < len; i += 32) alive += P.et_rnd[b + i] >= t;
+        for (int o = 16; o > 0; o >>= 1) alive += __shfl_xor_sync(0xffffffffu, alive, o);
+        const int32_t lost = prev - alive;
+        const int32_t need = shift ? (prev >> shift) : 1;
+        if (alive == len || lost < need) continue;
+        const int32_t a = g.eu[e], cv = g.ev[e];
+        int32_t out = 0;
+        for (int32_t i0 = 0; i0 < len; i0 += 32) {
+            const int32_t i = i0 + lane;
+            int32_t w = 0, id = 0, r = 0;
+            bool keep = false;
+            if (i < len) {
+                w = P.lw[b + i];
+                id = P.lt[b + i];
+                r = P.et_rnd[b + i];
+                keep = r >= t;
+            }
+            const unsigned mk = __ballot_sync(0xffffffffu, keep);
+            if (keep) {
+                const int32_t at = out + __popc(mk & nd_lanemask_lt());
+                P.lw[b + at] = w;
+                P.lt[b + at] = id;
+                P.et_rnd[b + at] = r;
+                const int x = w > cv ? 0 : (w > a ? 1 : 2);
+                P.ltp[3 * (int64_t)id + x] = at;
+            }
+            out += __popc(mk);
+        }
+        if (lane == 0) {
+            P.llen[e] = out;
+            P.lprev[e] = out;
+        }
+    }
+}
+
+template <typename CT>
+__global__ void k_contract34(GraphView g, PeelView<CT> P) { phase_contract34(g, P); }
+
 template <typename CT>
 __global__ void k_adv_min(PeelView<CT> P) { phase_adv_min(P); }
 template <typename CT>
@@ -716,6 +772,7 @@ struct Prep {
     int64_t h[3];  // (3,4): hash-table offset of the list, -1 when it is searched by bisection
     int32_t v[4];  // generic (r,s): the vertices of R
     const int32_t* lp;  // generic (r,s): the driving list
+    int32_t hk[3];      // (3,4): log2 of the slots of each list's hash table (from its original length)
 };
 
 // The light Update phase gives each warp one R at a time: its lanes share the R's lists and read
@@ -1011,17 +1068,20 @@ __device__ __forceinline__ void lists34(const GraphView& g, const PeelView<CT>& 
     for (int x = 0; x < 3; ++x) {
         int32_t e = g.tri_e[3 * (int64_t)R + x];
         q.b[x] = g.et_rp[e];
-        q.n[x] = g.et_rp[e + 1] - q.b[x];
-        q.h[x] = P.htab && nd_hashed(q.n[x]) ? P.hoff[e] : -1;
+        const int64_t n0 = g.et_rp[e + 1] - q.b[x];  // original length: it sizes the hash table
+        q.n[x] = g.llen ? (int64_t)g.llen[e] : n0;   // current length (after list contraction)
+        q.h[x] = P.htab && nd_hashed(n0) ? P.hoff[e] : -1;
+        q.hk[x] = q.h[x] >= 0 ? nd_hash_bits(n0) : 0;
     }
-    // sort the three lists by length
+    // sort the three lists by current length
 #pragma unroll
     for (int pass = 0; pass < 3; ++pass) {
         int i = pass == 2 ? 1 : 0, j = pass == 0 ? 1 : 2;  // compare-exchange (0,1), (0,2), (1,2)
         if (q.n[j] < q.n[i]) {
             int64_t tb = q.b[i], tn = q.n[i], th = q.h[i];
-            q.b[i] = q.b[j], q.n[i] = q.n[j], q.h[i] = q.h[j];
-            q.b[j] = tb, q.n[j] = tn, q.h[j] = th;
+            int32_t tk = q.hk[i];
+            q.b[i] = q.b[j], q.n[i] = q.n[j], q.h[i] = q.h[j], q.hk[i] = q.hk[j];
+            q.b[j] = tb, q.n[j] = tn, q.h[j] = th, q.hk[j] = tk;
         }
     }
 }
@@ -1037,7 +1097,7 @@ struct Upd34 {
     __device__ static bool look(const GraphView& g, const RoundEnv<CT>& E, const Q& q, int x, int32_t w,
                                 int32_t& id, int32_t& r) {
         if (q.h[x] >= 0) {
-            if (!nd_hash_find(E.P.htab + q.h[x], nd_hash_bits(q.n[x]), w, id, r)) return false;
+            if (!nd_hash_find(E.P.htab + q.h[x], q.hk[x], w, id, r)) return false;
         } else {
             int64_t i = nd_find(g.et_w + q.b[x], q.n[x], w);
             if (i < 0) return false;
@@ -1092,7 +1152,7 @@ struct Upd34 {
         if (!la && !lb) return;
         const NdHashSlot* t1 = E.P.htab + q.h[1];
         const NdHashSlot* t2 = E.P.htab + q.h[2];
-        const int k1 = nd_hash_bits(q.n[1]), k2 = nd_hash_bits(q.n[2]);
+        const int k1 = q.hk[1], k2 = q.hk[2];
         uint32_t sa1 = nd_hash_slot(wa, k1), sa2 = nd_hash_slot(wa, k2);
         uint32_t sb1 = nd_hash_slot(wb, k1), sb2 = nd_hash_slot(wb, k2);
         int4 pa1 = make_int4(-1, 0, 0, 0), pa2 = pa1, pb1 = pa1, pb2 = pa1;
@@ -1539,7 +1599,10 @@ __global__ void __launch_bounds__(512, 2) k_peel_loop(GraphView g, PeelView<CT> 
         if (c->done) return;  // every block reads the same value after the barrier
         tr = c->t;
         if (c->contract) {  // written only by serial steps
-            phase_contract(g, P);
+            if constexpr (k34)
+                phase_contract34(g, P);
+            else
+                phase_contract(g, P);
             if (!grid_barrier(c, target, NoSerial{})) return;
             book(6);
         }
@@ -1619,6 +1682,7 @@ void nd_peel_init(PeelCtl* ctl, int64_t n_r, int64_t max_rounds, cudaStream_t st
 template <typename CT>
 void nd_peel_contract(const GraphView& g, const PeelView<CT>& P, cudaStream_t st) {
     if (P.ccol) ND_K(k_contract<CT><<<peel_blocks(), kThreads, 0, st>>>(g, P));
+    if (P.lw) ND_K(k_contract34<CT><<<peel_blocks(), kThreads, 0, st>>>(g, P));
 }
 
 template <typename CT>

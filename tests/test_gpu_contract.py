@@ -1,5 +1,7 @@
 """Graph contraction for (2,3) (Section 5.6): the peel compacts the adjacency rows of vertices
-that lost edges, so later Updates do not walk peeled edges. It must not change any result.
+that lost edges, so later Updates do not walk peeled edges; for (3,4) the same is done to the
+triangle lists, whose entries of peeled triangles are removed (moving each kept entry's tag and
+offset along). Neither may change any result.
 
 Compared with the oracle element by element (cores, peel rounds, |A| and k per round, destroyed
 triangles, decrements) with contraction forced before every round (every row that lost an entry
@@ -63,3 +65,41 @@ def test_contraction_schedule_follows_the_paper(nd, ctx):
         assert st["contractions"] == want.rho - 1
     finally:
         nd.nd_graph_free(G)
+
+
+@pytest.mark.parametrize("gi", range(len(GRAPHS)))
+def test_list_contraction_parity_34(nd, ctx, gi):
+    g = GRAPHS[gi]()
+    for mode in (0, nd.ND_PEEL_PERSISTENT, nd.ND_PEEL_LOOP_GRAPH, nd.ND_NO_GRAPH):
+        for c in (nd.ND_CONTRACT_ALWAYS, 0, nd.ND_CONTRACT_OFF):
+            got = assert_parity(nd, ctx, g, 3, 4, flags=mode | c)
+            if c == nd.ND_CONTRACT_OFF:
+                assert got["st"]["contractions"] == 0
+            elif c == nd.ND_CONTRACT_ALWAYS and got["st"]["rho"] > 1:
+                assert got["st"]["contractions"] >= 1
+
+
+def test_list_contraction_with_dense_buckets_and_no_directory(nd):
+    """(3,4) list contraction next to the dense buckets, and without the hash directory (every
+    list bisected over its compacted length)."""
+    import torch
+
+    g = gg.rmat(12, 16, 0.57, 0.19, 0.19, seed=86)
+    ctx = nd.nd_ctx_create(0)
+    try:
+        for c in (nd.ND_CONTRACT_ALWAYS, 0):
+            assert_parity(nd, ctx, g, 3, 4, flags=nd.ND_DENSE_BUCKETS | c)
+    finally:
+        nd.nd_ctx_destroy(ctx)
+    alloc, free = nd.torch_allocator_hooks(0)
+
+    def small_only(nbytes, stream):
+        return 0 if nbytes > 16 << 20 else alloc(nbytes, stream)
+
+    ctx = nd.nd_ctx_create(0, stream=torch.cuda.Stream())
+    nd.nd_ctx_set_allocator(ctx, small_only, free)
+    try:
+        for c in (nd.ND_CONTRACT_ALWAYS, 0):
+            assert_parity(nd, ctx, g, 3, 4, flags=c)
+    finally:
+        nd.nd_ctx_destroy(ctx)
