@@ -18,6 +18,8 @@ Functions (each follows the passage named in its docstring):
 * ``certify(...)``              validity + elimination-order certificate of a claimed result
 * ``certify_all(...)``          the same certificate over every r-clique (or a sample), with the
                                 oracle's own id lookups, split across host threads
+* ``nuclei(g, r, s, core, c)``  the s-connected components of the c-(r,s) nucleus (Section 2,
+                                footnote: the original definition's connectivity)
 """
 from __future__ import annotations
 
@@ -77,6 +79,8 @@ def _L():
             lib.orc_certify_all.argtypes = g3 + [ctypes.c_int, ctypes.c_int, ctypes.c_int64, i32p, i32p, i64p,
                                                  ctypes.c_int64, i64p, ctypes.c_int64, ctypes.c_int, i64p, i64p, i64p]
             lib.orc_certify_all.restype = ctypes.c_int
+            lib.orc_nuclei.argtypes = g3 + [ctypes.c_int, ctypes.c_int, i32p, ctypes.c_int32, i32p, i64p]
+            lib.orc_nuclei.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -244,3 +248,16 @@ def certify_all(g, r: int, s: int, core: np.ndarray, rnd: np.ndarray, levels: np
         out["sup_valid"] = sv[:k]
         out["sup_order"] = so[:k]
     return out
+
+
+def nuclei(g, r: int, s: int, core: np.ndarray, level: int):
+    """(comp int32[n_r], n_components): comp[R] = smallest r-clique id of R's component among the
+    r-cliques with core >= level, joined through s-cliques all of whose r-subsets have core >=
+    level (Section 2, footnote); -1 where core < level."""
+    rp, col, a = _g(g)
+    core = np.ascontiguousarray(core, dtype=np.int32)
+    out = np.zeros(max(core.size, 1), np.int32)
+    nc = ctypes.c_int64()
+    _check(_L().orc_nuclei(*a, int(r), int(s), _p(core if core.size else np.zeros(1, np.int32), ctypes.c_int32),
+                           int(level), _p(out, ctypes.c_int32), ctypes.byref(nc)), "nuclei")
+    return out[: core.size], int(nc.value)

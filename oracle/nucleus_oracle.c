@@ -1257,3 +1257,80 @@ int orc_certify_all(int32_t n, const int64_t *rp, const int32_t *col, int r, int
         for (int i = 0; i < 4; ++i) bad[i] = nb[i];
     return err;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Connectivity of a nucleus (Section 2, footnote: the original definition also requires the     */
+/* r-cliques of a nucleus to be connected through s-cliques).                                    */
+/*
+ * For a level c, the r-cliques with core >= c form the c-(r,s) nucleus set X_c. Two of them are
+ * joined when some s-clique contains both and all of that s-clique's r-subsets lie in X_c; the
+ * connected nuclei at level c are the connected components of this relation. comp[R] receives the
+ * smallest r-clique id of R's component (or -1 when core[R] < c); *n_comp the number of components.
+ * Plain sequential union-find over every s-clique, listed once (Algorithm 1 growth).
+ */
+typedef struct {
+    const rtable *T;
+    int s;
+    const int32_t *core;
+    int32_t level;
+    int64_t *parent;
+    int bad;
+} nuc_ctx;
+
+static int64_t uf_root(int64_t *parent, int64_t x) {
+    while (parent[x] != x) x = parent[x];
+    return x;
+}
+
+static void nuc_func(void *vctx, const int32_t *S) {
+    nuc_ctx *K = (nuc_ctx *)vctx;
+    int64_t ids[128];
+    int k = subsets_of(K->T, K->s, S, ids);
+    for (int i = 0; i < k; ++i) {
+        if (ids[i] < 0) {
+            K->bad = 1;
+            return;
+        }
+        if (K->core[ids[i]] < K->level) return; /* S is not inside X_c */
+    }
+    for (int i = 1; i < k; ++i) {
+        int64_t a = uf_root(K->parent, ids[0]), b = uf_root(K->parent, ids[i]);
+        if (a == b) continue;
+        if (a < b)
+            K->parent[b] = a;
+        else
+            K->parent[a] = b;
+    }
+}
+
+int orc_nuclei(int32_t n, const int64_t *rp, const int32_t *col, int r, int s, const int32_t *core, int32_t level,
+               int32_t *comp, int64_t *n_comp) {
+    if (check_rs(r, s)) return -1;
+    og g = {n, rp, col};
+    rtable T;
+    if (rtable_build(&g, r, &T)) return -2;
+    int64_t nr = T.count;
+    int64_t *parent = (int64_t *)malloc((size_t)(nr > 0 ? nr : 1) * sizeof(int64_t));
+    if (!parent) {
+        free(T.t);
+        return -2;
+    }
+    for (int64_t i = 0; i < nr; ++i) parent[i] = i;
+    nuc_ctx K = {&T, s, core, level, parent, 0};
+    int rc = list_all(&g, s, nuc_func, &K);
+    int64_t nc = 0;
+    for (int64_t i = 0; i < nr; ++i) {
+        if (core[i] < level) {
+            comp[i] = -1;
+            continue;
+        }
+        int64_t root = uf_root(parent, i); /* the smallest id: unions always hang the larger root */
+        comp[i] = (int32_t)root;
+        if (root == i) nc++;
+    }
+    if (n_comp) *n_comp = nc;
+    free(parent);
+    free(T.t);
+    if (rc) return -2;
+    return K.bad ? -3 : 0;
+}

@@ -427,3 +427,71 @@ def test_certify_all_accepts_oracle_and_rejects_perturbations(r, s):
         res_s = orc.certify_all(g, r, s, d.core, d.round, d.levels, ids=np.arange(d.core.size))
         assert res_s["bad_valid"] == res_s["bad_order"] == res_s["bad_level"] == 0
         assert j >= 0
+
+
+# ------------------------------------------------------------------------------------
+# Connectivity of nuclei (Section 2, footnote): components against networkx and brute force
+
+def _brute_nuclei(g, r, s, core, level):
+    """Components by breadth-first search over r-cliques, two of them adjacent when a vertex
+    subset of size s that is pairwise adjacent contains both and has every r-subset at level."""
+    rcl = py_cliques(g, r)
+    pos = {t: i for i, t in enumerate(rcl)}
+    adj = {i: set() for i in range(len(rcl))}
+    for S in py_cliques(g, s):
+        ids = [pos[t] for t in itertools.combinations(S, r)]
+        if all(core[i] >= level for i in ids):
+            for a in ids:
+                adj[a].update(ids)
+    comp = np.full(len(rcl), -1, np.int32)
+    for i in range(len(rcl)):
+        if core[i] < level or comp[i] >= 0:
+            continue
+        stack, members = [i], []
+        comp[i] = i
+        while stack:
+            x = stack.pop()
+            members.append(x)
+            for y in adj[x]:
+                if comp[y] < 0:
+                    comp[y] = i
+                    stack.append(y)
+        comp[members] = min(members)
+    return comp
+
+
+def test_nuclei_12_equals_networkx_kcore_components():
+    for seed in range(4):
+        g = gg.chung_lu(400, 6.0, 2.2, seed=120 + seed)
+        G = to_nx(g)
+        core = orc.decompose(g, 1, 2).core
+        for level in sorted(set(core.tolist()))[:6]:
+            comp, nc = orc.nuclei(g, 1, 2, core, level)
+            H = G.subgraph([v for v in range(g.n) if core[v] >= level])
+            want = np.full(g.n, -1, np.int32)
+            for cc in nx.connected_components(H):
+                want[list(cc)] = min(cc)
+            assert np.array_equal(comp, want) and nc == nx.number_connected_components(H)
+
+
+@pytest.mark.parametrize("r,s", [(1, 2), (1, 3), (2, 3), (2, 4), (3, 4), (3, 5)])
+def test_nuclei_brute_force(r, s):
+    for seed in range(8):
+        g = gg.disjoint_union(gg.gnp(8, 0.6, 1300 + seed), gg.gnp(7, 0.7, 1400 + seed))
+        core = orc.decompose(g, r, s).core
+        for level in sorted(set(core.tolist())):
+            comp, nc = orc.nuclei(g, r, s, core, level)
+            want = _brute_nuclei(g, r, s, core, level)
+            assert np.array_equal(comp, want), (seed, r, s, level)
+            assert nc == len(set(want[want >= 0].tolist()))
+
+
+def test_nuclei_closed_forms():
+    # K_n: at its one level every r-clique is in one nucleus; two disjoint copies give two
+    g = gg.disjoint_union(gg.complete(6), gg.complete(6))
+    for r, s in [(1, 2), (2, 3), (3, 4)]:
+        core = orc.decompose(g, r, s).core
+        comp, nc = orc.nuclei(g, r, s, core, int(core.max()))
+        assert nc == 2 and np.all(comp >= 0)
+        comp, nc = orc.nuclei(g, r, s, core, int(core.max()) + 1)
+        assert nc == 0 and np.all(comp == -1)
