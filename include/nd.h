@@ -235,6 +235,21 @@ ND_API int nd_round_times(nd_graph *g, int64_t *ns_out, int64_t cap);
  * ND_PTR_DEVICE; NULL to query n_r only). r in {1, 2, 3, 4}. Errors: ND_EINVAL, ND_ENOMEM. */
 ND_API int nd_rcliques(nd_graph *g, int r, int32_t *tuples_out, int flags, int64_t *n_r_out);
 
+/* Connected nuclei at one level (Section 2, footnote: the definition of a c-(r,s) nucleus in
+ * the nucleus literature also asks that its r-cliques be connected through s-cliques; the
+ * paper's core numbers leave this out, and the nucleus hierarchy is built from it). core is
+ * the r-clique core number array of an nd_decompose(g, r, s) (n_r int32, canonical order, host
+ * or device with ND_PTR_DEVICE). X = the r-cliques with core >= level; two r-cliques of X are
+ * joined when some s-clique contains both and has all C(s,r) of its r-subsets in X.
+ * comp_out (n_r int32, same memory kind as core; nullable) receives, for each r-clique of X,
+ * the smallest canonical id in its component, and -1 for the r-cliques outside X;
+ * *n_comp_out (host, nullable) the number of components. Any core array is accepted (the
+ * relation is then taken over the X it defines). Errors: ND_EINVAL (NULL graph or core,
+ * unsupported (r,s)), ND_ENOMEM, ND_EOVERFLOW (more than INT32_MAX r-cliques), ND_EINTERNAL
+ * (a bounded union-find retry loop ran out, or an r-subset is missing from the index). */
+ND_API int nd_nuclei(nd_graph *g, int r, int s, const int32_t *core, int32_t level, int32_t *comp_out,
+                     int flags, int64_t *n_comp_out);
+
 /* ---- batches and serving --------------------------------------------------------------
  * Many independent graphs, each with its own (r,s). A batch merges the graphs that share an
  * (r,s) into one disjoint union and runs a single decomposition on it: the core number of an

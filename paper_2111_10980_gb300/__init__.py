@@ -42,7 +42,7 @@ STATUS_NAMES = {0: "ND_OK", 1: "ND_EINVAL", 2: "ND_ENOMEM", 3: "ND_EOVERFLOW", 4
 # every entry point declared in include/nd.h
 API = ["nd_ctx_create", "nd_ctx_set_allocator", "nd_ctx_set_limits", "nd_ctx_set_tuning", "nd_ctx_destroy", "nd_ctx_bytes_in_use", "nd_kernel_launches", "nd_last_error",
        "nd_load_csr", "nd_graph_free", "nd_graph_size", "nd_orient", "nd_graph_reset", "nd_count", "nd_decompose",
-       "nd_rounds", "nd_round_times", "nd_rcliques", "nd_batch_run", "nd_server_create", "nd_submit", "nd_poll", "nd_server_drain",
+       "nd_rounds", "nd_round_times", "nd_rcliques", "nd_nuclei", "nd_batch_run", "nd_server_create", "nd_submit", "nd_poll", "nd_server_drain",
        "nd_server_destroy", "nd_kcore_noalloc"]
 ND_NOALLOC_MAX_VERTICES = 262144
 
@@ -138,6 +138,7 @@ def lib() -> ctypes.CDLL:
         L.nd_rounds.argtypes = [vp, vp, vp, i64, i64p]
         L.nd_round_times.argtypes = [vp, vp, i64]
         L.nd_rcliques.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, i64p]
+        L.nd_nuclei.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, i32, vp, ctypes.c_int, i64p]
         L.nd_kcore_noalloc.argtypes = [i32, vp, vp, vp, vp]
         L.nd_batch_run.argtypes = [vp, ctypes.POINTER(nd_request), i32, ctypes.POINTER(nd_batch_stats)]
         L.nd_server_create.argtypes = [vp, ctypes.POINTER(nd_server_cfg), ctypes.POINTER(vp)]
@@ -368,6 +369,26 @@ def nd_rcliques(g: Handle, r: int, out=None):
     p, dev = _ptr(out)
     _check(lib().nd_rcliques(g.ptr, r, p, ND_PTR_DEVICE if dev else 0, ctypes.byref(n_r)))
     return out
+
+
+def nd_nuclei(g: Handle, r: int, s: int, core, level: int, out=None):
+    """Connected nuclei at `level` (nd.h: nd_nuclei): (comp, n_components), comp[i] = smallest
+    r-clique id of i's component among the r-cliques with core >= level, -1 elsewhere. core is
+    the core array of nd_decompose(g, r, s) (numpy or CUDA tensor); comp follows its kind."""
+    n = int(core.shape[0])
+    if out is None:
+        if _is_torch_cuda(core):
+            import torch
+            out = torch.empty(n, dtype=torch.int32, device=core.device)
+        else:
+            out = np.empty(n, np.int32)
+    pc, dev = _ptr(core)
+    po, dev_o = _ptr(out)
+    if dev != dev_o:
+        raise ValueError("core and out must both be host arrays or both CUDA tensors")
+    nc = ctypes.c_int64()
+    _check(lib().nd_nuclei(g.ptr, r, s, pc, int(level), po, ND_PTR_DEVICE if dev else 0, ctypes.byref(nc)))
+    return out, nc.value
 
 
 def nd_kcore_noalloc(rowptr, col, core_out, stream=None):
