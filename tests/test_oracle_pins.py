@@ -495,3 +495,12 @@ def test_nuclei_closed_forms():
         assert nc == 2 and np.all(comp >= 0)
         comp, nc = orc.nuclei(g, r, s, core, int(core.max()) + 1)
         assert nc == 0 and np.all(comp == -1)
+    # bowtie: two triangles sharing only vertex 0. As (1,2) it is one 2-core; as (2,3) each
+    # edge lies in one triangle (core 1), and no triangle holds edges of both, so two nuclei
+    bow = gg.csr_from_edges(5, np.array([0, 0, 1, 0, 0, 3], np.int32), np.array([1, 2, 2, 3, 4, 4], np.int32))
+    core = orc.decompose(bow, 1, 2).core
+    assert list(core) == [2] * 5 and orc.nuclei(bow, 1, 2, core, 2)[1] == 1
+    core = orc.decompose(bow, 2, 3).core
+    comp, nc = orc.nuclei(bow, 2, 3, core, 1)
+    # canonical edge ids: 01, 02, 03, 04, 12, 34
+    assert list(core) == [1] * 6 and nc == 2 and list(comp) == [0, 0, 2, 2, 0, 2]
