@@ -1130,63 +1130,158 @@ struct Upd34 {
         if (dec_live(r2, E.t)) after_dec(E, id2, o2);
     }
 
-    // Both search lists hashed: candidates j and j + 32 of this lane at once, each step issuing
-    // the loads of both before using any (the loop is bound by memory latency, so two chains in
-    // flight per lane nearly halve its time): list-0 entries, first probes of lists 1 and 2,
-    // then the decrements.
-    static constexpr bool kPair = true;
-    template <typename Q>
-    __device__ static void cand2(const GraphView& g, const RoundEnv<CT>& E, int32_t R, const Q& q, int64_t j,
-                                 UpdCounters& k) {
-        const int64_t b0 = q.b[0];
-        const bool vb = j + 32 < q.n[0];
-        int32_t ra = E.P.et_rnd[b0 + j], ia = g.et_t[b0 + j], wa = g.et_w[b0 + j];
-        int32_t rb = -1, ib = 0, wb = 0;
-        if (vb) {
-            rb = E.P.et_rnd[b0 + j + 32];
-            ib = g.et_t[b0 + j + 32];
-            wb = g.et_w[b0 + j + 32];
+    // Light Update over a group of at most 32 triangles of A, with a queue of candidates per warp.
+    // Lane l sets up triangle l of the group (its three lists, in parallel with the other lanes,
+    // instead of one dependent setup chain per triangle). The warp then reads the driving lists of
+    // the group's triangles one after another, coalesced, and drops the dead entries (triangle
+    // peeled in an earlier round, or a member of A with a smaller id than R) with one read each; the
+    // surviving candidates of any triangle of the group go to a shared-memory queue as (w, id, slot
+    // and state of the list-0 triangle). Whenever 64 are queued, every lane probes lists 1 and 2 for
+    // two of them and applies the decrements, so the probes and atomics run on full warps, two
+    // chains per lane, whatever mix of short and long lists the group has. A triangle whose lists 1
+    // and 2 are not both hashed is listed the per-candidate way after the queue is drained.
+    static constexpr bool kQueued = true;
+    static constexpr int kQueue = 96;  // < 64 entries before an append of at most 32
+    __device__ static void run_group(const GraphView& g, const RoundEnv<CT>& E, const int32_t* Ag, int nG,
+                                     int64_t heavy, UpdCounters& k, int32_t* qw, int32_t* qi, int32_t* qm) {
+        const unsigned full = 0xffffffffu;
+        const int lane = threadIdx.x & 31;
+        int32_t R = -1;
+        int64_t b0 = 0, h1 = 0, h2 = 0, n0 = 0;
+        int32_t hk = 0;
+        bool paired = false;
+        if (lane < nG) {
+            R = Ag[lane];
+            unmark_a(E.P, R);
+            Prep q;
+            lists34(g, E.P, R, q);
+            n0 = q.n[0];
+            b0 = q.b[0];
+            h1 = q.h[1];
+            h2 = q.h[2];
+            hk = q.hk[1] | (q.hk[2] << 8);
+            paired = h1 >= 0 && h2 >= 0;
+            if (n0 > heavy) {
+                unsigned slot = atomicAdd(&E.P.ctl->nH, 1u);
+                if (slot < E.P.hcap) {
+                    E.P.H[slot] = R;
+                    n0 = 0;  // the heavy phase lists it
+                }
+            }
         }
-        bool la = ra >= E.t && !(ra == E.t && ia < R);
-        bool lb = vb && rb >= E.t && !(rb == E.t && ib < R);
-        if (!la && !lb) return;
-        const NdHashSlot* t1 = E.P.htab + q.h[1];
-        const NdHashSlot* t2 = E.P.htab + q.h[2];
-        const int k1 = q.hk[1], k2 = q.hk[2];
-        uint32_t sa1 = nd_hash_slot(wa, k1), sa2 = nd_hash_slot(wa, k2);
-        uint32_t sb1 = nd_hash_slot(wb, k1), sb2 = nd_hash_slot(wb, k2);
+        int qn = 0;
+        unsigned todo = __ballot_sync(full, paired && n0 > 0);
+        while (todo) {
+            const int sl = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int32_t Rs = __shfl_sync(full, R, sl);
+            const int64_t bs = __shfl_sync(full, b0, sl), ns = __shfl_sync(full, n0, sl);
+            // entries of the next 32-wide chunk are loaded before the current one is filtered
+            int64_t j = lane;
+            int32_t r0 = -1, i0 = 0, w0 = 0;
+            if (j < ns) {
+                r0 = E.P.et_rnd[bs + j];
+                i0 = g.et_t[bs + j];
+                w0 = g.et_w[bs + j];
+            }
+            for (int64_t off = 0; off < ns; off += 32) {
+                const int64_t jn = off + 32 + lane;
+                int32_t r1 = -1, i1 = 0, w1 = 0;
+                if (jn < ns) {
+                    r1 = E.P.et_rnd[bs + jn];
+                    i1 = g.et_t[bs + jn];
+                    w1 = g.et_w[bs + jn];
+                }
+                const bool keep = r0 >= E.t && !(r0 == E.t && i0 < Rs);
+                const unsigned m = __ballot_sync(full, keep);
+                if (keep) {
+                    const int at = qn + __popc(m & nd_lanemask_lt());
+                    qw[at] = w0;
+                    qi[at] = i0;
+                    qm[at] = sl | (r0 == E.t ? 32 : 0) | (dec_live(r0, E.t) ? 64 : 0);
+                }
+                qn += __popc(m);
+                if (qn >= 64) {
+                    __syncwarp();
+                    drain(E, R, h1, h2, hk, qw + qn - 64, qi + qn - 64, qm + qn - 64, 64, k);
+                    qn -= 64;
+                    __syncwarp();
+                }
+                r0 = r1, i0 = i1, w0 = w1;
+            }
+        }
+        if (qn > 0) {
+            __syncwarp();
+            drain(E, R, h1, h2, hk, qw, qi, qm, qn, k);
+            __syncwarp();
+        }
+        // triangles with a list that is not hashed: one at a time, per candidate
+        unsigned rest = __ballot_sync(full, !paired && n0 > 0);
+        while (rest) {
+            const int sl = __ffs(rest) - 1;
+            rest &= rest - 1;
+            const int32_t Rs = __shfl_sync(full, R, sl);
+            Prep q;
+            lists34(g, E.P, Rs, q);
+            for (int64_t jj = lane; jj < q.n[0]; jj += 32) cand(g, E, Rs, q, jj, k);
+        }
+    }
+
+    // Probes and decrements of nq <= 64 queued candidates: lane l takes entries l and l + 32.
+    // The group's per-triangle state (R, hash offsets and sizes of lists 1 and 2) is read from the
+    // lane that set the triangle up.
+    __device__ static void drain(const RoundEnv<CT>& E, int32_t R, int64_t h1, int64_t h2, int32_t hk,
+                                 const int32_t* qw, const int32_t* qi, const int32_t* qm, int nq, UpdCounters& k) {
+        const unsigned full = 0xffffffffu;
+        const int lane = threadIdx.x & 31;
+        bool la = lane < nq, lb = lane + 32 < nq;
+        const int32_t wa = la ? qw[lane] : 0, ia = la ? qi[lane] : 0, ma = la ? qm[lane] : 0;
+        const int32_t wb = lb ? qw[lane + 32] : 0, ib = lb ? qi[lane + 32] : 0, mb = lb ? qm[lane + 32] : 0;
+        const int sa = ma & 31, sb = mb & 31;
+        const int32_t Ra = __shfl_sync(full, R, sa), Rb = __shfl_sync(full, R, sb);
+        const int64_t a1 = __shfl_sync(full, h1, sa), a2 = __shfl_sync(full, h2, sa);
+        const int64_t c1 = __shfl_sync(full, h1, sb), c2 = __shfl_sync(full, h2, sb);
+        const int32_t ka = __shfl_sync(full, hk, sa), kb = __shfl_sync(full, hk, sb);
+        const int ka1 = ka & 255, ka2 = ka >> 8, kb1 = kb & 255, kb2 = kb >> 8;
+        const NdHashSlot* ta1 = E.P.htab + a1;
+        const NdHashSlot* ta2 = E.P.htab + a2;
+        const NdHashSlot* tb1 = E.P.htab + c1;
+        const NdHashSlot* tb2 = E.P.htab + c2;
+        uint32_t sa1 = nd_hash_slot(wa, ka1), sa2 = nd_hash_slot(wa, ka2);
+        uint32_t sb1 = nd_hash_slot(wb, kb1), sb2 = nd_hash_slot(wb, kb2);
         int4 pa1 = make_int4(-1, 0, 0, 0), pa2 = pa1, pb1 = pa1, pb2 = pa1;
         if (la) {
-            pa1 = *reinterpret_cast<const int4*>(t1 + sa1);
-            pa2 = *reinterpret_cast<const int4*>(t2 + sa2);
+            pa1 = *reinterpret_cast<const int4*>(ta1 + sa1);
+            pa2 = *reinterpret_cast<const int4*>(ta2 + sa2);
         }
         if (lb) {
-            pb1 = *reinterpret_cast<const int4*>(t1 + sb1);
-            pb2 = *reinterpret_cast<const int4*>(t2 + sb2);
+            pb1 = *reinterpret_cast<const int4*>(tb1 + sb1);
+            pb2 = *reinterpret_cast<const int4*>(tb2 + sb2);
         }
         int32_t ia1 = 0, ra1 = 0, ia2 = 0, ra2 = 0, ib1 = 0, rb1 = 0, ib2 = 0, rb2 = 0;
-        la = la && nd_hash_resolve(t1, k1, wa, sa1, pa1, ia1, ra1) && nd_hash_resolve(t2, k2, wa, sa2, pa2, ia2, ra2);
-        lb = lb && nd_hash_resolve(t1, k1, wb, sb1, pb1, ib1, rb1) && nd_hash_resolve(t2, k2, wb, sb2, pb2, ib2, rb2);
-        la = la && ra1 >= E.t && !(ra1 == E.t && ia1 < R) && ra2 >= E.t && !(ra2 == E.t && ia2 < R);
-        lb = lb && rb1 >= E.t && !(rb1 == E.t && ib1 < R) && rb2 >= E.t && !(rb2 == E.t && ib2 < R);
+        la = la && nd_hash_resolve(ta1, ka1, wa, sa1, pa1, ia1, ra1) && nd_hash_resolve(ta2, ka2, wa, sa2, pa2, ia2, ra2);
+        lb = lb && nd_hash_resolve(tb1, kb1, wb, sb1, pb1, ib1, rb1) && nd_hash_resolve(tb2, kb2, wb, sb2, pb2, ib2, rb2);
+        la = la && ra1 >= E.t && !(ra1 == E.t && ia1 < Ra) && ra2 >= E.t && !(ra2 == E.t && ia2 < Ra);
+        lb = lb && rb1 >= E.t && !(rb1 == E.t && ib1 < Rb) && rb2 >= E.t && !(rb2 == E.t && ib2 < Rb);
         // decrements of both 4-cliques go out before any result is looked at
-        int64_t oa0 = la && dec_live(ra, E.t) ? nd_atomic_dec(&E.P.cnt[ia]) : 0;
+        const bool da0 = la && (ma & 64), db0 = lb && (mb & 64);
+        int64_t oa0 = da0 ? nd_atomic_dec(&E.P.cnt[ia]) : 0;
         int64_t oa1 = la && dec_live(ra1, E.t) ? nd_atomic_dec(&E.P.cnt[ia1]) : 0;
         int64_t oa2 = la && dec_live(ra2, E.t) ? nd_atomic_dec(&E.P.cnt[ia2]) : 0;
-        int64_t ob0 = lb && dec_live(rb, E.t) ? nd_atomic_dec(&E.P.cnt[ib]) : 0;
+        int64_t ob0 = db0 ? nd_atomic_dec(&E.P.cnt[ib]) : 0;
         int64_t ob1 = lb && dec_live(rb1, E.t) ? nd_atomic_dec(&E.P.cnt[ib1]) : 0;
         int64_t ob2 = lb && dec_live(rb2, E.t) ? nd_atomic_dec(&E.P.cnt[ib2]) : 0;
         if (la) {
             k.listed++;
-            k.decs += (ra != E.t) + (ra1 != E.t) + (ra2 != E.t);
-            if (dec_live(ra, E.t)) after_dec(E, ia, oa0);
+            k.decs += !(ma & 32) + (ra1 != E.t) + (ra2 != E.t);
+            if (da0) after_dec(E, ia, oa0);
             if (dec_live(ra1, E.t)) after_dec(E, ia1, oa1);
             if (dec_live(ra2, E.t)) after_dec(E, ia2, oa2);
         }
         if (lb) {
             k.listed++;
-            k.decs += (rb != E.t) + (rb1 != E.t) + (rb2 != E.t);
-            if (dec_live(rb, E.t)) after_dec(E, ib, ob0);
+            k.decs += !(mb & 32) + (rb1 != E.t) + (rb2 != E.t);
+            if (db0) after_dec(E, ib, ob0);
             if (dec_live(rb1, E.t)) after_dec(E, ib1, ob1);
             if (dec_live(rb2, E.t)) after_dec(E, ib2, ob2);
         }
@@ -1223,15 +1318,6 @@ struct UpdGen {
 };
 
 template <typename U, typename = void>
-struct has_pair {
-    static constexpr bool value = false;
-};
-template <typename U>
-struct has_pair<U, decltype((void)U::kPair)> {
-    static constexpr bool value = U::kPair;
-};
-
-template <typename U, typename = void>
 struct is_staged {
     static constexpr bool value = false;
 };
@@ -1240,6 +1326,15 @@ struct is_staged<U, decltype((void)U::kStaged)> {
     static constexpr bool value = U::kStaged;
 };
 
+
+template <typename U, typename = void>
+struct is_queued {
+    static constexpr bool value = false;
+};
+template <typename U>
+struct is_queued<U, decltype((void)U::kQueued)> {
+    static constexpr bool value = U::kQueued;
+};
 
 template <typename U, typename = void>
 struct heavy_work {
@@ -1309,6 +1404,19 @@ __device__ void phase_update(const GraphView& g, const PeelView<CT>& P) {
             Stage24 stg{s_w[wid], s_x[wid], s_y[wid], s_b[wid], s_p[wid]};
             U::run_warp(g, E, R, k, stg);
         }
+    } else if constexpr (is_queued<U>::value) {
+        // groups of up to 32 r-cliques per warp with a queue of live candidates (Upd34::run_group);
+        // chunks of at most 32, about nA / (4 warps) each, so that small rounds still spread
+        __shared__ int32_t s_qw[kMaxWarpsPerBlock][U::kQueue], s_qi[kMaxWarpsPerBlock][U::kQueue],
+            s_qm[kMaxWarpsPerBlock][U::kQueue];
+        unsigned long long per = (unsigned long long)nwarps() * 4ull;
+        unsigned chunk = (unsigned)(E.nA / per);
+        chunk = chunk < 1u ? 1u : (chunk > 32u ? 32u : chunk);
+        const int64_t heavy = heavy_limit<U>(P);
+        for (unsigned i0 = take_chunk(P.ctl, chunk); i0 < E.nA; i0 = take_chunk(P.ctl, chunk)) {
+            int nG = (int)(E.nA - i0 < chunk ? E.nA - i0 : chunk);
+            U::run_group(g, E, E.A + i0, nG, heavy, k, s_qw[wid], s_qi[wid], s_qm[wid]);
+        }
     } else {
         // one warp per r-clique: its lanes read the driving list coalesced
         const unsigned chunk = update_chunk(E.nA);
@@ -1328,12 +1436,6 @@ __device__ void phase_update(const GraphView& g, const PeelView<CT>& P) {
                     }
                 }
                 if (__shfl_sync(full, queued, 0)) continue;
-            }
-            if constexpr (has_pair<U>::value) {
-                if (q.h[1] >= 0 && q.h[2] >= 0) {
-                    for (int64_t j = lane; j < n0; j += 64) U::cand2(g, E, R, q, j, k);
-                    continue;
-                }
             }
             for (int64_t j = lane; j < n0; j += 32) U::cand(g, E, R, q, j, k);
         }
