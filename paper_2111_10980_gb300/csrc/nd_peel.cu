@@ -631,33 +631,50 @@ __device__ void phase_sort_count(const PeelView<CT>& P) {
     if (threadIdx.x == 0) c->hist[blockIdx.x] = total;
 }
 
+// Each warp writes the ids of its own slice of the block's words in order: its offset is the
+// members of the blocks before (their counts, summed by the whole block) plus those of the warps
+// before it in this block (recounted from the bitmap, which the count pass left in L2); inside the
+// slice a warp scan places 32 words at a time, with no block-wide barrier per step.
 template <typename CT>
 __device__ void phase_sort_write(const PeelView<CT>& P) {
     PeelCtl* c = P.ctl;
     int64_t w0, w1;
     sort_range(c, w0, w1);
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int64_t per = (w1 - w0 + nw - 1) / nw;
+    int64_t a = w0 + wid * per, b = a + per < w1 ? a + per : w1;
+    if (a > b) a = b;
+    unsigned cnt = 0;
+    for (int64_t w = a + lane; w < b; w += 32) cnt += __popc(P.abits[w]);
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(full, cnt, o);
+    unsigned prior = 0;
+    for (unsigned x = threadIdx.x; x < blockIdx.x; x += blockDim.x) prior += (unsigned)c->hist[x];
+    unsigned excl;
+    const unsigned blocks_before = block_excl_sum(prior, excl);
+    block_excl_sum(lane == 0 ? cnt : 0u, excl);
+    unsigned long long at = (unsigned long long)blocks_before + __shfl_sync(full, excl, 0);
     int32_t* A = pick(P.A, c->wa);
-    unsigned long long at = c->hist[blockIdx.x];
-    for (int64_t base = w0; base < w1; base += blockDim.x) {
-        int64_t w = base + threadIdx.x;
-        uint32_t bits = w < w1 ? P.abits[w] : 0u;
-        unsigned excl;
-        unsigned total = block_excl_sum(__popc(bits), excl);
-        unsigned long long o = at + excl;
+    for (int64_t base = a; base < b; base += 32) {
+        const int64_t w = base + lane;
+        uint32_t bits = w < b ? P.abits[w] : 0u;
+        const unsigned pc = __popc(bits);
+        unsigned inc = pc;
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned y = __shfl_up_sync(full, inc, o);
+            if (lane >= o) inc += y;
+        }
+        unsigned long long o = at + inc - pc;
         while (bits) {
-            int b = __ffs(bits) - 1;
+            int bit = __ffs(bits) - 1;
             bits &= bits - 1;
-            if (o < P.cap) A[o] = (int32_t)(w * 32 + b);
+            if (o < P.cap) A[o] = (int32_t)(w * 32 + bit);
             ++o;
         }
-        at += total;
+        at += __shfl_sync(full, inc, 31);
     }
 }
 
-template <typename CT>
-__global__ void k_sort_count(PeelView<CT> P) { phase_sort_count(P); }
-template <typename CT>
-__global__ void k_sort_write(PeelView<CT> P) { phase_sort_write(P); }
 
 // ------------------------------------------------------------------------------------
 // Update
@@ -1136,12 +1153,13 @@ struct Upd34 {
     // the group's triangles one after another, coalesced, and drops the dead entries (triangle
     // peeled in an earlier round, or a member of A with a smaller id than R) with one read each; the
     // surviving candidates of any triangle of the group go to a shared-memory queue as (w, id, slot
-    // and state of the list-0 triangle). Whenever 64 are queued, every lane probes lists 1 and 2 for
-    // two of them and applies the decrements, so the probes and atomics run on full warps, two
-    // chains per lane, whatever mix of short and long lists the group has. A triangle whose lists 1
+    // and state of the list-0 triangle). Whenever 32 kIlp are queued, every lane probes lists 1 and 2
+    // for kIlp of them and applies the decrements, so the probes and atomics run on full warps
+    // whatever mix of short and long lists the group has. A triangle whose lists 1
     // and 2 are not both hashed is listed the per-candidate way after the queue is drained.
     static constexpr bool kQueued = true;
-    static constexpr int kQueue = 96;  // < 64 entries before an append of at most 32
+    static constexpr int kIlp = 1;                // queued candidates per lane and drain
+    static constexpr int kQueue = 32 * kIlp + 32;  // < 32 kIlp entries before an append of at most 32
     __device__ static void run_group(const GraphView& g, const RoundEnv<CT>& E, const int32_t* Ag, int nG,
                                      int64_t heavy, UpdCounters& k, int32_t* qw, int32_t* qi, int32_t* qm) {
         const unsigned full = 0xffffffffu;
@@ -1201,10 +1219,11 @@ struct Upd34 {
                     qm[at] = sl | (r0 == E.t ? 32 : 0) | (dec_live(r0, E.t) ? 64 : 0);
                 }
                 qn += __popc(m);
-                if (qn >= 64) {
+                if (qn >= 32 * kIlp) {
                     __syncwarp();
-                    drain(E, R, h1, h2, hk, qw + qn - 64, qi + qn - 64, qm + qn - 64, 64, k);
-                    qn -= 64;
+                    const int d = qn - 32 * kIlp;
+                    drain(E, R, h1, h2, hk, qw + d, qi + d, qm + d, 32 * kIlp, k);
+                    qn = d;
                     __syncwarp();
                 }
                 r0 = r1, i0 = i1, w0 = w1;
@@ -1227,63 +1246,71 @@ struct Upd34 {
         }
     }
 
-    // Probes and decrements of nq <= 64 queued candidates: lane l takes entries l and l + 32.
+    // Probes and decrements of nq <= 32 kIlp queued candidates: lane l takes entries l, l + 32, ...
+    // (kIlp chains in flight per lane: every load of a step is issued before any result is used).
     // The group's per-triangle state (R, hash offsets and sizes of lists 1 and 2) is read from the
     // lane that set the triangle up.
     __device__ static void drain(const RoundEnv<CT>& E, int32_t R, int64_t h1, int64_t h2, int32_t hk,
                                  const int32_t* qw, const int32_t* qi, const int32_t* qm, int nq, UpdCounters& k) {
+        constexpr int N = kIlp;
         const unsigned full = 0xffffffffu;
         const int lane = threadIdx.x & 31;
-        bool la = lane < nq, lb = lane + 32 < nq;
-        const int32_t wa = la ? qw[lane] : 0, ia = la ? qi[lane] : 0, ma = la ? qm[lane] : 0;
-        const int32_t wb = lb ? qw[lane + 32] : 0, ib = lb ? qi[lane + 32] : 0, mb = lb ? qm[lane + 32] : 0;
-        const int sa = ma & 31, sb = mb & 31;
-        const int32_t Ra = __shfl_sync(full, R, sa), Rb = __shfl_sync(full, R, sb);
-        const int64_t a1 = __shfl_sync(full, h1, sa), a2 = __shfl_sync(full, h2, sa);
-        const int64_t c1 = __shfl_sync(full, h1, sb), c2 = __shfl_sync(full, h2, sb);
-        const int32_t ka = __shfl_sync(full, hk, sa), kb = __shfl_sync(full, hk, sb);
-        const int ka1 = ka & 255, ka2 = ka >> 8, kb1 = kb & 255, kb2 = kb >> 8;
-        const NdHashSlot* ta1 = E.P.htab + a1;
-        const NdHashSlot* ta2 = E.P.htab + a2;
-        const NdHashSlot* tb1 = E.P.htab + c1;
-        const NdHashSlot* tb2 = E.P.htab + c2;
-        uint32_t sa1 = nd_hash_slot(wa, ka1), sa2 = nd_hash_slot(wa, ka2);
-        uint32_t sb1 = nd_hash_slot(wb, kb1), sb2 = nd_hash_slot(wb, kb2);
-        int4 pa1 = make_int4(-1, 0, 0, 0), pa2 = pa1, pb1 = pa1, pb2 = pa1;
-        if (la) {
-            pa1 = *reinterpret_cast<const int4*>(ta1 + sa1);
-            pa2 = *reinterpret_cast<const int4*>(ta2 + sa2);
+        bool live[N];
+        int32_t w[N], id0[N], me[N], Rx[N], k1[N], k2[N], i1[N], r1[N], i2[N], r2[N];
+        const NdHashSlot* t1[N];
+        const NdHashSlot* t2[N];
+        uint32_t s1[N], s2[N];
+        int4 p1[N], p2[N];
+#pragma unroll
+        for (int x = 0; x < N; ++x) {
+            const int e = lane + 32 * x;
+            live[x] = e < nq;
+            w[x] = live[x] ? qw[e] : 0;
+            id0[x] = live[x] ? qi[e] : 0;
+            me[x] = live[x] ? qm[e] : 0;
+            const int sl = me[x] & 31;
+            Rx[x] = __shfl_sync(full, R, sl);
+            t1[x] = E.P.htab + __shfl_sync(full, h1, sl);
+            t2[x] = E.P.htab + __shfl_sync(full, h2, sl);
+            const int32_t kk = __shfl_sync(full, hk, sl);
+            k1[x] = kk & 255;
+            k2[x] = kk >> 8;
+            s1[x] = nd_hash_slot(w[x], k1[x]);
+            s2[x] = nd_hash_slot(w[x], k2[x]);
         }
-        if (lb) {
-            pb1 = *reinterpret_cast<const int4*>(tb1 + sb1);
-            pb2 = *reinterpret_cast<const int4*>(tb2 + sb2);
+#pragma unroll
+        for (int x = 0; x < N; ++x) {
+            p1[x] = make_int4(-1, 0, 0, 0);
+            p2[x] = p1[x];
+            if (live[x]) {
+                p1[x] = *reinterpret_cast<const int4*>(t1[x] + s1[x]);
+                p2[x] = *reinterpret_cast<const int4*>(t2[x] + s2[x]);
+            }
         }
-        int32_t ia1 = 0, ra1 = 0, ia2 = 0, ra2 = 0, ib1 = 0, rb1 = 0, ib2 = 0, rb2 = 0;
-        la = la && nd_hash_resolve(ta1, ka1, wa, sa1, pa1, ia1, ra1) && nd_hash_resolve(ta2, ka2, wa, sa2, pa2, ia2, ra2);
-        lb = lb && nd_hash_resolve(tb1, kb1, wb, sb1, pb1, ib1, rb1) && nd_hash_resolve(tb2, kb2, wb, sb2, pb2, ib2, rb2);
-        la = la && ra1 >= E.t && !(ra1 == E.t && ia1 < Ra) && ra2 >= E.t && !(ra2 == E.t && ia2 < Ra);
-        lb = lb && rb1 >= E.t && !(rb1 == E.t && ib1 < Rb) && rb2 >= E.t && !(rb2 == E.t && ib2 < Rb);
-        // decrements of both 4-cliques go out before any result is looked at
-        const bool da0 = la && (ma & 64), db0 = lb && (mb & 64);
-        int64_t oa0 = da0 ? nd_atomic_dec(&E.P.cnt[ia]) : 0;
-        int64_t oa1 = la && dec_live(ra1, E.t) ? nd_atomic_dec(&E.P.cnt[ia1]) : 0;
-        int64_t oa2 = la && dec_live(ra2, E.t) ? nd_atomic_dec(&E.P.cnt[ia2]) : 0;
-        int64_t ob0 = db0 ? nd_atomic_dec(&E.P.cnt[ib]) : 0;
-        int64_t ob1 = lb && dec_live(rb1, E.t) ? nd_atomic_dec(&E.P.cnt[ib1]) : 0;
-        int64_t ob2 = lb && dec_live(rb2, E.t) ? nd_atomic_dec(&E.P.cnt[ib2]) : 0;
-        if (la) {
+        int64_t o0[N], o1[N], o2[N];
+#pragma unroll
+        for (int x = 0; x < N; ++x) {
+            i1[x] = r1[x] = i2[x] = r2[x] = 0;
+            live[x] = live[x] && nd_hash_resolve(t1[x], k1[x], w[x], s1[x], p1[x], i1[x], r1[x]) &&
+                      nd_hash_resolve(t2[x], k2[x], w[x], s2[x], p2[x], i2[x], r2[x]);
+            live[x] = live[x] && r1[x] >= E.t && !(r1[x] == E.t && i1[x] < Rx[x]) && r2[x] >= E.t &&
+                      !(r2[x] == E.t && i2[x] < Rx[x]);
+        }
+        // the decrements of every 4-clique go out before any result is looked at
+#pragma unroll
+        for (int x = 0; x < N; ++x) {
+            o0[x] = live[x] && (me[x] & 64) ? nd_atomic_dec(&E.P.cnt[id0[x]]) : 0;
+            o1[x] = live[x] && dec_live(r1[x], E.t) ? nd_atomic_dec(&E.P.cnt[i1[x]]) : 0;
+            o2[x] = live[x] && dec_live(r2[x], E.t) ? nd_atomic_dec(&E.P.cnt[i2[x]]) : 0;
+        }
+#pragma unroll
+        for (int x = 0; x < N; ++x) {
+            if (!live[x]) continue;
             k.listed++;
-            k.decs += !(ma & 32) + (ra1 != E.t) + (ra2 != E.t);
-            if (da0) after_dec(E, ia, oa0);
-            if (dec_live(ra1, E.t)) after_dec(E, ia1, oa1);
-            if (dec_live(ra2, E.t)) after_dec(E, ia2, oa2);
-        }
-        if (lb) {
-            k.listed++;
-            k.decs += !(mb & 32) + (rb1 != E.t) + (rb2 != E.t);
-            if (db0) after_dec(E, ib, ob0);
-            if (dec_live(rb1, E.t)) after_dec(E, ib1, ob1);
-            if (dec_live(rb2, E.t)) after_dec(E, ib2, ob2);
+            k.decs += !(me[x] & 32) + (r1[x] != E.t) + (r2[x] != E.t);
+            if (me[x] & 64) after_dec(E, id0[x], o0[x]);
+            if (dec_live(r1[x], E.t)) after_dec(E, i1[x], o1[x]);
+            if (dec_live(r2[x], E.t)) after_dec(E, i2[x], o2[x]);
         }
     }
 };
@@ -1621,19 +1648,6 @@ struct SortDecide {
     __device__ void operator()() const { decide_sort(c, P); }
 };
 
-// per-block member counts (hist[0 .. gridDim)) -> exclusive offsets
-struct SortScan {
-    PeelCtl* c;
-    __device__ void operator()() const {
-        unsigned long long run = 0;
-        for (unsigned b = 0; b < gridDim.x; ++b) {
-            unsigned long long v = c->hist[b];
-            c->hist[b] = run;
-            run += v;
-        }
-    }
-};
-
 // after the light Update: finish the round now unless heavy r-cliques are waiting
 template <typename CT>
 struct CtlUnlessHeavy {
@@ -1727,7 +1741,7 @@ __global__ void __launch_bounds__(512, 2) k_peel_loop(GraphView g, PeelView<CT> 
         }
         if (c->sorta) {
             phase_sort_count(P);
-            if (!grid_barrier(c, target, SortScan{c})) return;
+            if (!grid_barrier(c, target, NoSerial{})) return;
             phase_sort_write(P);
             if (!grid_barrier(c, target, NoSerial{})) return;
             book(3);
