@@ -694,7 +694,7 @@ static int build_tri_hash(nd_graph* g, DBuf& hoff, DBuf& htab, DBuf& hpos) {
     if (!rc) rc = nd_alloc(c, htab, sizeof(NdHashSlot) * std::max<int64_t>(total, 1));
     if (!rc) rc = nd_alloc(c, hpos, sizeof(int32_t) * std::max<int64_t>(3 * g->n3, 1));
     if (rc) return rc;
-    ND_CUDA(cudaMemsetAsync(htab.p, 0xff, htab.bytes, st));
+    // every table is written whole by the fill kernels (free slots all ones): no clearing pass
     ND_CUDA(cudaMemsetAsync(hpos.p, 0xff, hpos.bytes, st));
     nd_tri_hash_fill(v, (const int64_t*)hoff.p, (NdHashSlot*)htab.p, (int32_t*)hpos.p, st);
     return nd_check_launch("triangle hash");

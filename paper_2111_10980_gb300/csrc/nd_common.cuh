@@ -76,44 +76,64 @@ __device__ __forceinline__ int64_t nd_append(unsigned int* counter, int32_t* lis
     return slot;
 }
 
-// Windowed warp merge of two ascending lists (all 32 lanes call it with the same arguments).
-// Each step holds A[a .. a+32) and B[b .. b+32) in registers, lane i owning A[a+i] and B[b+i]
-// (INT32_MAX past the ends). Every lane finds the lower bound of its A element in the B window
-// with a 5-step search over shuffles; then the window with the smaller last element moves on
-// (both on a tie). Every element is loaded once, coalesced, and every common element is seen
-// exactly once, in the step whose windows hold both copies. visit(lane_active, ia, ib) is called
-// by every lane at every step; when lane_active is true, A[ia] == B[ib] is a common element.
-template <typename Visit>
-__device__ __forceinline__ void nd_warp_merge(const int32_t* __restrict__ A, int64_t na, const int32_t* __restrict__ B,
-                                              int64_t nb, Visit visit) {
-    const unsigned full = 0xffffffffu;
-    int lane = threadIdx.x & 31;
-    int64_t a = 0, b = 0;
-    int32_t av = lane < na ? __ldg(A + lane) : 0x7fffffff;
-    int32_t bv = lane < nb ? __ldg(B + lane) : 0x7fffffff;
-    while (a < na && b < nb) {
-        int la = (int)((na - a < 32 ? na - a : 32) - 1);
-        int lb = (int)((nb - b < 32 ? nb - b : 32) - 1);
-        int32_t amax = __shfl_sync(full, av, la);
-        int32_t bmax = __shfl_sync(full, bv, lb);
-        int lo = 0;
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-            int32_t probe = __shfl_sync(full, bv, lo + step - 1);
-            if (probe < av) lo += step;
-        }
-        int32_t hit = __shfl_sync(full, bv, lo);
-        bool found = lane <= la && hit == av;
-        visit(found, a + lane, b + lo);
-        if (amax <= bmax) {
-            a += 32;
-            av = a + lane < na ? __ldg(A + a + lane) : 0x7fffffff;
-        }
-        if (bmax <= amax) {
-            b += 32;
-            bv = b + lane < nb ? __ldg(B + b + lane) : 0x7fffffff;
-        }
+// Merge path over two ascending lists of distinct ids, A before B on ties: the warp splits the
+// merged order into 32 runs of equal length, one per lane. nd_merge_run finds where the lane's run
+// starts by bisecting its diagonal; nd_merge_walk walks the run one element per step and calls
+// visit(i, j, w) for every common element w = A[i] = B[j], in ascending order within the lane.
+// Each common element is met in exactly one run (the one that consumes its copy in A: B's next
+// element is then the smallest not below it). About (na + nb) / 32 steps per lane, one load each.
+// Indices are 32-bit (list lengths are below 2^31).
+struct NdMergeRun {
+    int i, j, steps;
+};
+
+__device__ __forceinline__ NdMergeRun nd_merge_run(const int32_t* __restrict__ A, int na, const int32_t* __restrict__ B,
+                                                   int nb) {
+    const int lane = threadIdx.x & 31;
+    const int total = na + nb, per = (total + 31) >> 5;
+    int d = lane * per;
+    if (d > total) d = total;
+    const int dend = d + per < total ? d + per : total;
+    // i = how many of the first d merged elements come from A
+    int lo = d > nb ? d - nb : 0, hi = d < na ? d : na;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(A + mid) <= __ldg(B + d - 1 - mid))
+            lo = mid + 1;
+        else
+            hi = mid;
     }
+    return NdMergeRun{lo, d - lo, dend - d};
+}
+
+template <typename Visit>
+__device__ __forceinline__ void nd_merge_walk(const int32_t* __restrict__ A, int na, const int32_t* __restrict__ B,
+                                              int nb, NdMergeRun r, Visit visit) {
+    constexpr int32_t kEnd = 0x7fffffff;  // past a list's end (no vertex id)
+    int i = r.i, j = r.j;
+    int32_t av = i < na ? __ldg(A + i) : kEnd, bv = j < nb ? __ldg(B + j) : kEnd;
+    for (int step = 0; step < r.steps; ++step) {
+        const bool ta = av <= bv;
+        if (ta && av == bv) visit(i, j, av);
+        if (ta)
+            ++i;
+        else
+            ++j;
+        const int idx = ta ? i : j, lim = ta ? na : nb;
+        const int32_t nv = idx < lim ? __ldg((ta ? A : B) + idx) : kEnd;
+        if (ta)
+            av = nv;
+        else
+            bv = nv;
+    }
+}
+
+// |A ∩ B| counted by this lane's run (sum over the warp for the whole intersection)
+__device__ __forceinline__ int nd_merge_count(const int32_t* __restrict__ A, int na, const int32_t* __restrict__ B,
+                                              int nb) {
+    int c = 0;
+    nd_merge_walk(A, na, B, nb, nd_merge_run(A, na, B, nb), [&](int, int, int32_t) { ++c; });
+    return c;
 }
 
 // Hash directory of the triangle lists (built for a (3,4) peel): list L(e) with more than

@@ -36,49 +36,6 @@ __device__ __forceinline__ int warp_sum(int v) {
     return v;
 }
 
-// |A ∩ B| of two ascending lists of distinct ids by merge path: the warp splits the merged order
-// (A before B on ties) into 32 equal runs of consecutive positions; each lane finds where its run
-// starts by bisecting its diagonal, then merges its run one element per step, counting an element
-// of A when it is consumed while equal to B's next element. Each element of A is consumed in exactly
-// one run, so every common id is counted once. About (na + nb) / 32 steps per lane, each one load
-// and a few instructions (a windowed warp merge spends a shuffle bisection per 32 elements).
-// Indices are 32-bit (list lengths are below 2^31).
-__device__ __forceinline__ int merge_count(const int32_t* __restrict__ A, int na, const int32_t* __restrict__ B,
-                                           int nb) {
-    constexpr int32_t kEnd = 0x7fffffff;  // past a list's end (no vertex id)
-    const int lane = threadIdx.x & 31;
-    const int total = na + nb, per = (total + 31) >> 5;
-    int d = lane * per;
-    if (d > total) d = total;
-    const int dend = d + per < total ? d + per : total;
-    // i = how many of the first d merged elements come from A
-    int lo = d > nb ? d - nb : 0, hi = d < na ? d : na;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (__ldg(A + mid) <= __ldg(B + d - 1 - mid))
-            lo = mid + 1;
-        else
-            hi = mid;
-    }
-    int i = lo, j = d - lo, c = 0;
-    int32_t av = i < na ? __ldg(A + i) : kEnd, bv = j < nb ? __ldg(B + j) : kEnd;
-    for (int step = d; step < dend; ++step) {
-        const bool ta = av <= bv;
-        c += (ta && av == bv) ? 1 : 0;
-        if (ta)
-            ++i;
-        else
-            ++j;
-        const int idx = ta ? i : j, lim = ta ? na : nb;
-        const int32_t nv = idx < lim ? __ldg((ta ? A : B) + idx) : kEnd;
-        if (ta)
-            av = nv;
-        else
-            bv = nv;
-    }
-    return c;
-}
-
 template <typename CT>
 __global__ void k_count12(GraphView g, CT* __restrict__ cnt) {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < g.n; v += (int64_t)gridDim.x * blockDim.x)
@@ -104,7 +61,7 @@ __global__ void k_count23(GraphView g, CT* __restrict__ cnt) {
         }
         int c = 0;
         if (nd_prefer_merge(nx, ny))
-            c = merge_count(xs, (int)nx, ys, (int)ny);
+            c = nd_merge_count(xs, (int)nx, ys, (int)ny);
         else
             for (int64_t i = lane; i < nx; i += 32) c += nd_find(ys, ny, xs[i]) >= 0 ? 1 : 0;
         c = warp_sum(c);
@@ -140,7 +97,7 @@ __global__ void k_count34(GraphView g, CT* __restrict__ cnt) {
         int c = 0;
         const bool probe = g.htab && nd_hashed(n1) && n1 > 2 * n0 + 64;
         if (!probe && nd_prefer_merge(n0, n1)) {
-            c = merge_count(g.et_w + b0, (int)n0, g.et_w + b1, (int)n1);
+            c = nd_merge_count(g.et_w + b0, (int)n0, g.et_w + b1, (int)n1);
         } else if (probe) {
             // the long list has a hash directory: one probe instead of a bisection
             const NdHashSlot* tab = g.htab + g.hoff[e1];

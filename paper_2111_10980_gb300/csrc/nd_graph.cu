@@ -161,11 +161,10 @@ __global__ void k_edge_support(GraphView g, int64_t* __restrict__ sigma, int64_t
         }
         int c = 0, cu = 0;
         if (nd_prefer_merge(nx, ny)) {
-            nd_warp_merge(xs, nx, ys, ny, [&](bool f, int64_t ix, int64_t) {
-                if (f) {
-                    c++;
-                    cu += (xs[ix] > b) ? 1 : 0;
-                }
+            const int ix = (int)nx, iy = (int)ny;
+            nd_merge_walk(xs, ix, ys, iy, nd_merge_run(xs, ix, ys, iy), [&](int, int, int32_t w) {
+                c++;
+                cu += w > b ? 1 : 0;
             });
         } else {
             for (int64_t i = lane; i < nx; i += 32) {
@@ -202,39 +201,48 @@ __global__ void k_edge_fill(GraphView g, const int64_t* __restrict__ et_rp, cons
         int64_t out = et_rp[e];
         int64_t sig = et_rp[e + 1] - out;
         int64_t split_e = sig - (tbase[e + 1] - tbase[e]);
-        int64_t pos = 0;
-        // writes the common element at driver position p and other-list position q (q < 0: none)
-        auto emit = [&](bool hit, int64_t p, int64_t q) {
-            unsigned m = __ballot_sync(0xffffffffu, hit);
-            if (hit) {
-                int32_t w = g.col[p];
-                int64_t local = pos + __popc(m & nd_lanemask_lt());
-                int64_t pa = a_drives ? p : q;  // position of w in N(a)
-                int64_t pb = a_drives ? q : p;  // position of w in N(b)
-                int32_t e_aw = g.pos2e[pa], e_bw = g.pos2e[pb];
-                et_w[out + local] = w;
-                if (w > b) {
-                    int64_t tid = tbase[e] + (local - split_e);
-                    et_t[out + local] = (int32_t)tid;
-                    tri_e[3 * tid + 0] = (int32_t)e;
-                    tri_e[3 * tid + 1] = e_aw;
-                    tri_e[3 * tid + 2] = e_bw;
-                    tri_pos[3 * tid + 0] = (int32_t)local;
-                } else {
-                    et_t[out + local] = e_aw;
-                }
+        // writes common element w, found at driver position p and other-list position q, as entry
+        // `local` of L(a,b)
+        auto put = [&](int64_t local, int64_t p, int64_t q, int32_t w) {
+            int64_t pa = a_drives ? p : q;  // position of w in N(a)
+            int64_t pb = a_drives ? q : p;  // position of w in N(b)
+            int32_t e_aw = g.pos2e[pa], e_bw = g.pos2e[pb];
+            et_w[out + local] = w;
+            if (w > b) {
+                int64_t tid = tbase[e] + (local - split_e);
+                et_t[out + local] = (int32_t)tid;
+                tri_e[3 * tid + 0] = (int32_t)e;
+                tri_e[3 * tid + 1] = e_aw;
+                tri_e[3 * tid + 2] = e_bw;
+                tri_pos[3 * tid + 0] = (int32_t)local;
+            } else {
+                et_t[out + local] = e_aw;
             }
-            pos += __popc(m);
         };
         if (nd_prefer_merge(xe - xb, ye - yb)) {
-            nd_warp_merge(g.col + xb, xe - xb, g.col + yb, ye - yb,
-                          [&](bool f, int64_t ix, int64_t iy) { emit(f, xb + ix, yb + iy); });
+            // merge path: count this lane's matches, place them after the lower lanes' (exclusive
+            // scan), then walk the run again and write them
+            const int32_t *X = g.col + xb, *Y = g.col + yb;
+            const int nx = (int)(xe - xb), ny = (int)(ye - yb);
+            const NdMergeRun run = nd_merge_run(X, nx, Y, ny);
+            int cnt = 0;
+            nd_merge_walk(X, nx, Y, ny, run, [&](int, int, int32_t) { ++cnt; });
+            int inc = cnt;
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            int64_t local = inc - cnt;
+            nd_merge_walk(X, nx, Y, ny, run, [&](int i, int j, int32_t w) { put(local++, xb + i, yb + j, w); });
         } else {
+            int64_t pos = 0;
             for (int64_t p0 = xb; p0 < xe; p0 += 32) {
                 int64_t p = p0 + lane;
                 int64_t q = -1;
                 if (p < xe) q = nd_find(g.col + yb, ye - yb, g.col[p]);
-                emit(q >= 0, p, q >= 0 ? yb + q : -1);
+                unsigned m = __ballot_sync(0xffffffffu, q >= 0);
+                if (q >= 0) put(pos + __popc(m & nd_lanemask_lt()), p, yb + q, g.col[p]);
+                pos += __popc(m);
             }
         }
     }
@@ -359,8 +367,68 @@ __global__ void k_tri_hash_sizes(GraphView g, int64_t* __restrict__ slots) {
     }
 }
 
-// one warp per long list; each entry claims a free slot by compare-and-swap on its (w, id) half,
-// then sets the round field to unpeeled and records the slot for its triangle (hpos)
+// Filling one list's table: each entry claims a free slot by compare-and-swap on its (w, id) pair,
+// its round is set to unpeeled and the slot is recorded for its triangle (hpos). A free slot is
+// all ones. The triangle's edges are (xy, xz, yz) for x < y < z: e = (a, c) is xy when w > c, xz
+// when a < w < c, yz when w < a.
+__device__ __forceinline__ int hash_which(int32_t w, int32_t a, int32_t c) { return w > c ? 0 : (w > a ? 1 : 2); }
+
+// Tables of at most 2^kHashSmemBits slots are built in shared memory, (w, id) pairs only, by one
+// block per list, and written out whole and coalesced (free slots included), so the directory
+// needs no clearing and the compare-and-swaps stay on chip. Each block collects the lists of
+// 256 consecutive edges that qualify and then fills them one after another.
+constexpr int kHashSmemBits = 13;  // 8,192 slots: 64 KiB of (w, id) pairs
+constexpr int kHashBlock = 256;
+
+__global__ void __launch_bounds__(kHashBlock) k_tri_hash_fill_smem(GraphView g, const int64_t* __restrict__ hoff,
+                                                                    NdHashSlot* __restrict__ tab,
+                                                                    int32_t* __restrict__ hpos) {
+    extern __shared__ unsigned long long s_tab[];
+    __shared__ int64_t s_list[kHashBlock];
+    __shared__ int s_cnt;
+    for (int64_t base = (int64_t)blockIdx.x * kHashBlock; base < g.m; base += (int64_t)gridDim.x * kHashBlock) {
+        if (threadIdx.x == 0) s_cnt = 0;
+        __syncthreads();
+        const int64_t e0 = base + threadIdx.x;
+        if (e0 < g.m) {
+            int64_t n = g.et_rp[e0 + 1] - g.et_rp[e0];
+            if (nd_hashed(n) && nd_hash_bits(n) <= kHashSmemBits) s_list[atomicAdd(&s_cnt, 1)] = e0;
+        }
+        __syncthreads();
+        const int cnt = s_cnt;
+        for (int q = 0; q < cnt; ++q) {
+            const int64_t e = s_list[q];
+            const int64_t b = g.et_rp[e], n = g.et_rp[e + 1] - b;
+            const int k = nd_hash_bits(n);
+            const uint32_t S = 1u << k, mask = S - 1u;
+            for (uint32_t i = threadIdx.x; i < S; i += kHashBlock) s_tab[i] = ~0ull;
+            __syncthreads();
+            const int32_t a = g.eu[e], c = g.ev[e];
+            for (int64_t p = threadIdx.x; p < n; p += kHashBlock) {
+                const int32_t w = g.et_w[b + p], id = g.et_t[b + p];
+                const unsigned long long key = ((unsigned long long)(uint32_t)id << 32) | (uint32_t)w;
+                uint32_t sl = nd_hash_slot(w, k);
+                for (uint32_t probes = 0; probes <= mask; ++probes) {
+                    if (atomicCAS(&s_tab[sl], ~0ull, key) == ~0ull) {
+                        hpos[3 * (int64_t)id + hash_which(w, a, c)] = (int32_t)sl;
+                        break;
+                    }
+                    sl = (sl + 1) & mask;
+                }
+            }
+            __syncthreads();
+            int4* out = reinterpret_cast<int4*>(tab + hoff[e]);
+            for (uint32_t i = threadIdx.x; i < S; i += kHashBlock) {
+                const unsigned long long v = s_tab[i];
+                out[i] = v == ~0ull ? make_int4(-1, -1, -1, -1)
+                                    : make_int4((int32_t)(uint32_t)v, (int32_t)(v >> 32), ND_UNPEELED, -1);
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Larger tables: one warp per list clears its table, then claims slots in global memory.
 __global__ void k_tri_hash_fill(GraphView g, const int64_t* __restrict__ hoff, NdHashSlot* __restrict__ tab,
                                 int32_t* __restrict__ hpos) {
     int lane = threadIdx.x & 31;
@@ -369,21 +437,22 @@ __global__ void k_tri_hash_fill(GraphView g, const int64_t* __restrict__ hoff, N
         int64_t b = g.et_rp[e], n = g.et_rp[e + 1] - b;
         if (!nd_hashed(n)) continue;
         int k = nd_hash_bits(n);
+        if (k <= kHashSmemBits) continue;
         uint32_t mask = (1u << k) - 1u;
         NdHashSlot* t = tab + hoff[e];
+        int4* t4 = reinterpret_cast<int4*>(t);
+        for (uint32_t i = lane; i <= mask; i += 32) t4[i] = make_int4(-1, -1, -1, -1);
+        __syncwarp();
         const int32_t a = g.eu[e], c = g.ev[e];  // e = (a, c), a < c
         for (int64_t p = lane; p < n; p += 32) {
             int32_t w = g.et_w[b + p], id = g.et_t[b + p];
-            // the triangle's edges are (xy, xz, yz) for x < y < z: e is xy when w > c, xz when
-            // a < w < c, yz when w < a
-            int x = w > c ? 0 : (w > a ? 1 : 2);
             unsigned long long key = ((unsigned long long)(uint32_t)id << 32) | (uint32_t)w;  // little endian: w first
             uint32_t s = nd_hash_slot(w, k);
             for (uint32_t probes = 0; probes <= mask; ++probes) {
                 unsigned long long* half = reinterpret_cast<unsigned long long*>(t + s);
                 if (atomicCAS(half, 0xffffffffffffffffull, key) == 0xffffffffffffffffull) {
                     t[s].rnd = ND_UNPEELED;
-                    hpos[3 * (int64_t)id + x] = (int32_t)s;
+                    hpos[3 * (int64_t)id + hash_which(w, a, c)] = (int32_t)s;
                     break;
                 }
                 s = (s + 1) & mask;
@@ -401,6 +470,11 @@ void nd_tri_hash_sizes(const GraphView& g, int64_t* slots, cudaStream_t st) {
 
 void nd_tri_hash_fill(const GraphView& g, const int64_t* hoff, NdHashSlot* tab, int32_t* hpos, cudaStream_t st) {
     if (g.m <= 0) return;
+    const int smem = (int)sizeof(unsigned long long) << kHashSmemBits;
+    cudaFuncSetAttribute(k_tri_hash_fill_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int64_t want = (g.m + kHashBlock - 1) / kHashBlock, cap = (int64_t)nd_sm_count() * 3;
+    int blocks = (int)(want < cap ? (want > 0 ? want : 1) : cap);
+    ND_K(k_tri_hash_fill_smem<<<blocks, kHashBlock, smem, st>>>(g, hoff, tab, hpos));
     ND_K(k_tri_hash_fill<<<blocks_for_warps(g.m), kThreads, 0, st>>>(g, hoff, tab, hpos));
 }
 
