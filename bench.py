@@ -406,12 +406,12 @@ def per_rs_summary(stats, rs):
 # scale 17): the traffic of these kernels grows with the s-cliques listed. Keyed by the fingerprint
 # of the library sources the captures were taken on; reported only while the sources still match.
 NCU_TRAFFIC = {
-    # R-MAT scale 17 (n_4 = 819,091,962): k_peel_loop (3,4) 229.36 GB read + 34.92 GB written, k_count34
-    # 31.93 GB + 0.42 GB; scaled by 16,996,482,431 / 819,091,962 = 20.750. The (2,3) kernels are not
+    # R-MAT scale 17 (n_4 = 819,091,962): k_peel_loop (3,4) 247.32 GB read + 39.48 GB written, k_count34
+    # 54.31 GB + 0.55 GB; scaled by 16,996,482,431 / 819,091,962 = 20.750. The (2,3) kernels are not
     # listed: at scale 17 their arrays fit in L2, so their DRAM bytes do not scale.
-    "5796564e13eca883": {
-        ("rmat20", "k_peel_loop(3,4)"): 5.4840e+12,
-        ("rmat20", "k_count34"): 6.7129e+11,
+    "febbab31385947cb": {
+        ("rmat20", "k_peel_loop(3,4)"): 5.9513e+12,
+        ("rmat20", "k_count34"): 1.1384e+12,
     },
 }
 
