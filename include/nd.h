@@ -116,6 +116,9 @@ typedef struct nd_stats {
                             whenever at least 2n edges were peeled since the previous one, compacting
                             the adjacency rows that lost at least a quarter of their entries since
                             then; (3,4) the same for the triangle lists, once 2m triangles were peeled */
+    double t_hash_ms;   /* (3,4): the part of t_count_ms spent building the hash directory of the
+                           triangle lists (0 otherwise); the counting kernel itself took
+                           t_count_ms - t_hash_ms */
 } nd_stats;
 
 /* ---- context ------------------------------------------------------------------------- */

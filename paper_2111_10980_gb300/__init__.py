@@ -60,7 +60,7 @@ class nd_stats(ctypes.Structure):
                 ("t_orient_ms", ctypes.c_double), ("t_index_ms", ctypes.c_double), ("t_count_ms", ctypes.c_double),
                 ("t_peel_ms", ctypes.c_double), ("t_total_ms", ctypes.c_double), ("decrements", ctypes.c_int64),
                 ("t_phase_ms", ctypes.c_double * 6), ("t_contract_ms", ctypes.c_double),
-                ("contractions", ctypes.c_int64)]
+                ("contractions", ctypes.c_int64), ("t_hash_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}

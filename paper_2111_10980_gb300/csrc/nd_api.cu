@@ -1011,11 +1011,12 @@ int nd_decompose_dev(nd_graph* g, int r, int s, int count_width, int flags, Peel
     ND_TRY(nd_prepare(g, r, s, &n_r, &t_or, &t_ix));
     int w = 0;
     ND_TRY(nd_pick_width(g, r, s, count_width, &w));
-    cudaEvent_t e0, e1, e2, e3;
+    cudaEvent_t e0, e1, e2, e3, eh;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventCreate(&e2);
     cudaEventCreate(&e3);
+    cudaEventCreate(&eh);
     DBuf cnt;
     int rc = nd_alloc(c, po.core, 4 * std::max<int64_t>(n_r, 1));
     if (!rc) rc = nd_alloc(c, po.rnd, 4 * std::max<int64_t>(n_r, 1));
@@ -1030,6 +1031,7 @@ int nd_decompose_dev(nd_graph* g, int r, int s, int count_width, int flags, Peel
             rc = ND_OK;
         }
     }
+    cudaEventRecord(eh, c->stream);
     if (!rc) rc = nd_count_into(g, r, s, w, n_r, cnt);
     cudaEventRecord(e1, c->stream);
     unsigned long long tot = 0;
@@ -1038,11 +1040,13 @@ int nd_decompose_dev(nd_graph* g, int r, int s, int count_width, int flags, Peel
     if (!rc) rc = (w == 8) ? run_peel<int64_t>(g, r, s, cnt, n_r, flags, po) : run_peel<int32_t>(g, r, s, cnt, n_r, flags, po);
     cudaEventRecord(e2, c->stream);
     if (!rc) rc = nd_sync(c, "nd_decompose");
-    float tc = 0, tp = 0;
+    float tc = 0, tp = 0, th = 0;
     if (!rc) {
         cudaEventElapsedTime(&tc, e0, e1);
         cudaEventElapsedTime(&tp, e3, e2);
+        cudaEventElapsedTime(&th, e0, eh);
     }
+    cudaEventDestroy(eh);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaEventDestroy(e2);
@@ -1066,6 +1070,7 @@ int nd_decompose_dev(nd_graph* g, int r, int s, int count_width, int flags, Peel
     S.t_orient_ms = t_or;
     S.t_index_ms = t_ix;
     S.t_count_ms = tc;
+    S.t_hash_ms = (r == 3 && s == 4) ? th : 0.0;
     S.t_peel_ms = tp;
     S.t_total_ms = t_or + t_ix + tc + tp;
     if (st) *st = S;

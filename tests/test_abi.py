@@ -71,3 +71,29 @@ def test_error_path_without_gpu():
     assert L.nd_graph_free(None) == nd.ND_OK
     assert L.nd_orient(None, 0) == nd.ND_EINVAL
     assert L.nd_decompose(None, 2, 3, 0, None, None, 0, None) == nd.ND_EINVAL
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The binding's ctypes structures have the header's size and field offsets (compiled as C)."""
+    import ctypes
+
+    import paper_2111_10980_gb300 as nd
+
+    structs = {"nd_stats": nd.nd_stats, "nd_request": nd.nd_request, "nd_batch_stats": nd.nd_batch_stats,
+               "nd_server_cfg": nd.nd_server_cfg, "nd_result": nd.nd_result}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "nd.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l}
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)
