@@ -261,3 +261,39 @@ def nuclei(g, r: int, s: int, core: np.ndarray, level: int):
     _check(_L().orc_nuclei(*a, int(r), int(s), _p(core if core.size else np.zeros(1, np.int32), ctypes.c_int32),
                            int(level), _p(out, ctypes.c_int32), ctypes.byref(nc)), "nuclei")
     return out[: core.size], int(nc.value)
+
+
+def hierarchy(g, r: int, s: int, core: np.ndarray):
+    """The nucleus hierarchy (Section 2, footnote), written out from its definition level by level.
+
+    For every distinct core value c, the connected c-(r,s) nuclei are the components of
+    X_c = {R : core[R] >= c} (`nuclei`). A node of the hierarchy is a component of X_c that holds an
+    r-clique whose core number is exactly c; each r-clique belongs to the node of its own core
+    number. The parent of node (c, C) is the node (c', C') at the largest distinct level c' < c for
+    which the component C' of X_c' containing C holds an r-clique of core exactly c'. Returns
+    (comp, parent_level, parent_comp), int32[n_r] each: comp[R] = smallest r-clique id of R's
+    node's component; parent_level[R], parent_comp[R] = the level and smallest id of the parent
+    node of R's node, -1 and -1 for a root node."""
+    core = np.ascontiguousarray(core, dtype=np.int32)
+    n_r = core.size
+    comp = np.full(n_r, -1, np.int32)
+    parent_level = np.full(n_r, -1, np.int32)
+    parent_comp = np.full(n_r, -1, np.int32)
+    if n_r == 0:
+        return comp, parent_level, parent_comp
+    levels = np.unique(core)  # ascending
+    comps = {int(c): nuclei(g, r, s, core, int(c))[0] for c in levels}
+    # nodes at each level: the components that hold an r-clique of exactly that core number
+    nodes = {int(c): set(comps[int(c)][core == c].tolist()) for c in levels}
+    for R in range(n_r):
+        c = int(core[R])
+        comp[R] = comps[c][R]
+    for R in range(n_r):
+        c = int(core[R])
+        for c2 in reversed([int(x) for x in levels if x < c]):
+            cc = int(comps[c2][R])
+            if cc in nodes[c2]:
+                parent_level[R] = c2
+                parent_comp[R] = cc
+                break
+    return comp, parent_level, parent_comp

@@ -504,3 +504,88 @@ def test_nuclei_closed_forms():
     comp, nc = orc.nuclei(bow, 2, 3, core, 1)
     # canonical edge ids: 01, 02, 03, 04, 12, 34
     assert list(core) == [1] * 6 and nc == 2 and list(comp) == [0, 0, 2, 2, 0, 2]
+
+
+def _hierarchy_from_components(core, comp_at):
+    """Checks the defining properties of a hierarchy output against per-level components
+    comp_at[c] (smallest id per component, -1 outside X_c), computed independently."""
+    levels = sorted(set(core.tolist()))
+    nodes = {c: set(comp_at[c][core == c].tolist()) for c in levels}
+    return levels, nodes
+
+
+def _check_hierarchy(core, out, comp_at):
+    comp, plev, pcomp = out
+    levels, nodes = _hierarchy_from_components(core, comp_at)
+    for R in range(core.size):
+        c = int(core[R])
+        # the node of R: its component at its own level, which holds an r-clique of core c
+        assert comp[R] == comp_at[c][R] and comp[R] in nodes[c]
+        below = [x for x in levels if x < c and comp_at[x][R] in nodes[x]]
+        if not below:
+            assert plev[R] == -1 and pcomp[R] == -1
+            continue
+        # the parent is the nearest lower node, and its component contains R's component
+        assert plev[R] == max(below) and pcomp[R] == comp_at[plev[R]][R]
+        members = np.flatnonzero(comp_at[c] == comp[R])
+        assert np.all(comp_at[plev[R]][members] == pcomp[R])
+
+
+def test_hierarchy_closed_forms():
+    # Figure 1 as (1,2): the K5 (core 4) inside f's 3-core inside g's 2-core, a chain of three
+    g = gg.fig1()
+    core = orc.decompose(g, 1, 2).core
+    comp, plev, pcomp = orc.hierarchy(g, 1, 2, core)
+    assert list(core) == [4, 4, 4, 4, 4, 3, 2]
+    assert list(comp) == [0] * 7 and list(plev) == [3] * 5 + [2, -1] and list(pcomp) == [0] * 6 + [-1]
+    # Figure 1 as (3,4): cdg (core 0, in no 4-clique) is a node and a root of its own; the K5's
+    # triangles (core 2) hang under the level-1 node of abf, aef, bef
+    core = orc.decompose(g, 3, 4).core
+    comp, plev, pcomp = orc.hierarchy(g, 3, 4, core)
+    one = core == 1
+    assert core[13] == 0 and comp[13] == 13 and plev[13] == -1
+    assert np.all(plev[one] == -1) and np.all(plev[core == 2] == 1) and np.all(pcomp[core == 2] == 0)
+    # two K5s (vertices 0-4, 5-9) joined through a vertex x = 10 of degree 2: as (1,2) two level-4
+    # nodes, both children of the level-2 node that x closes
+    u = [a for a in range(5) for b in range(a + 1, 5)]
+    v = [b for a in range(5) for b in range(a + 1, 5)]
+    uu = np.array(u + [a + 5 for a in u] + [0, 5], np.int32)
+    vv = np.array(v + [b + 5 for b in v] + [10, 10], np.int32)
+    g2 = gg.csr_from_edges(11, uu, vv)
+    core = orc.decompose(g2, 1, 2).core
+    comp, plev, pcomp = orc.hierarchy(g2, 1, 2, core)
+    assert list(core) == [4] * 10 + [2]
+    assert list(comp) == [0] * 5 + [5] * 5 + [0]
+    assert list(plev) == [2] * 10 + [-1] and list(pcomp) == [0] * 10 + [-1]
+    # the same graph as (2,3): every K5 edge has core 3 and the two connector edges core 0. No
+    # triangle holds a connector, so each is a component of X_0 by itself (a level-0 node and a
+    # root); the K5s' components of X_0 hold no core-0 edge, so the two level-3 nodes are roots too
+    core = orc.decompose(g2, 2, 3).core
+    comp, plev, pcomp = orc.hierarchy(g2, 2, 3, core)
+    assert sorted(set(core.tolist())) == [0, 3]
+    assert np.all(plev == -1) and len(set(comp.tolist())) == 4
+
+
+@pytest.mark.parametrize("r,s", [(1, 2), (2, 3), (2, 4), (3, 4)])
+def test_hierarchy_brute_force(r, s):
+    # components from explicitly enumerated s-cliques (breadth-first search), not from the oracle
+    for seed in range(6):
+        g = gg.disjoint_union(gg.gnp(8, 0.6, 1500 + seed), gg.gnp(7, 0.75, 1600 + seed), gg.complete(s + 1))
+        core = orc.decompose(g, r, s).core
+        comp_at = {int(c): _brute_nuclei(g, r, s, core, int(c)) for c in set(core.tolist())}
+        _check_hierarchy(core, orc.hierarchy(g, r, s, core), comp_at)
+
+
+def test_hierarchy_12_networkx():
+    for seed in range(3):
+        g = gg.chung_lu(300, 6.0, 2.2, seed=170 + seed)
+        G = to_nx(g)
+        core = orc.decompose(g, 1, 2).core
+        comp_at = {}
+        for c in set(core.tolist()):
+            H = G.subgraph([v for v in range(g.n) if core[v] >= c])
+            want = np.full(g.n, -1, np.int32)
+            for cc in nx.connected_components(H):
+                want[list(cc)] = min(cc)
+            comp_at[int(c)] = want
+        _check_hierarchy(core, orc.hierarchy(g, 1, 2, core), comp_at)
