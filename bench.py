@@ -409,11 +409,16 @@ NCU_TRAFFIC = {
     # R-MAT scale 17 (n_4 = 819,091,962): k_peel_loop (3,4) 247.50 GB read + 39.52 GB written, k_count34
     # 54.53 GB + 0.56 GB; scaled by 16,996,482,431 / 819,091,962 = 20.750. The (2,3) kernels are not
     # listed: at scale 17 their arrays fit in L2, so their DRAM bytes do not scale.
-    "4ae0cc1de504de1f": {
+    "37514f67ef4c48be": {
         ("rmat20", "k_peel_loop(3,4)"): 5.9558e+12,
         ("rmat20", "k_count34"): 1.1432e+12,
     },
 }
+
+
+# translation units that no kernel of the timed step includes or calls (the connected nuclei and the
+# hierarchy, run outside the step): a change there leaves the captured kernels' traffic as it was
+NOT_IN_STEP = ("nd_nuclei.cu",)
 
 
 def sources_fingerprint():
@@ -422,6 +427,8 @@ def sources_fingerprint():
 
     h = hashlib.sha256()
     for f in sorted(glob.glob(os.path.join(ROOT, "paper_2111_10980_gb300", "csrc", "*"))):
+        if os.path.basename(f) in NOT_IN_STEP:
+            continue
         if f.endswith((".cu", ".cuh", ".h")):
             h.update(os.path.basename(f).encode())
             with open(f, "rb") as fh:

@@ -253,6 +253,23 @@ ND_API int nd_rcliques(nd_graph *g, int r, int32_t *tuples_out, int flags, int64
 ND_API int nd_nuclei(nd_graph *g, int r, int s, const int32_t *core, int32_t level, int32_t *comp_out,
                      int flags, int64_t *n_comp_out);
 
+/* The nucleus hierarchy (Section 2, footnote: the nested connected nuclei of all levels). For
+ * each distinct core number c, the connected nuclei at level c are the components of X_c as in
+ * nd_nuclei; a node of the hierarchy is such a component that holds an r-clique of core exactly
+ * c, and every r-clique belongs to the node of its own core number. The parent of node (c, C) is
+ * the node (c', C') at the largest distinct level c' < c whose component C' (of X_c') contains C;
+ * nodes without one are roots (the hierarchy is a forest). core: as for nd_nuclei (values in
+ * [0, 2^26)). Outputs, n_r int32 each, canonical order, same memory kind as core: comp_out[R] =
+ * the smallest r-clique id of the component of R's node; parent_level_out[R] and
+ * parent_comp_out[R] = the level and smallest id of the parent node of R's node, -1 and -1 for a
+ * root. With host pointers any output may be NULL; with ND_PTR_DEVICE all three are required.
+ * *n_nodes_out (host, nullable): the number of nodes. Cost: every s-clique is listed once over all
+ * levels (one union-find over the r-cliques, levels taken in decreasing order). Errors:
+ * ND_EINVAL (NULL graph or core, unsupported (r,s), a core value outside [0, 2^26)),
+ * ND_ENOMEM, ND_EOVERFLOW (more than INT32_MAX r-cliques), ND_EINTERNAL (as for nd_nuclei). */
+ND_API int nd_hierarchy(nd_graph *g, int r, int s, const int32_t *core, int32_t *comp_out, int32_t *parent_level_out,
+                        int32_t *parent_comp_out, int flags, int64_t *n_nodes_out);
+
 /* ---- batches and serving --------------------------------------------------------------
  * Many independent graphs, each with its own (r,s). A batch merges the graphs that share an
  * (r,s) into one disjoint union and runs a single decomposition on it: the core number of an

@@ -42,7 +42,7 @@ STATUS_NAMES = {0: "ND_OK", 1: "ND_EINVAL", 2: "ND_ENOMEM", 3: "ND_EOVERFLOW", 4
 # every entry point declared in include/nd.h
 API = ["nd_ctx_create", "nd_ctx_set_allocator", "nd_ctx_set_limits", "nd_ctx_set_tuning", "nd_ctx_destroy", "nd_ctx_bytes_in_use", "nd_kernel_launches", "nd_last_error",
        "nd_load_csr", "nd_graph_free", "nd_graph_size", "nd_orient", "nd_graph_reset", "nd_count", "nd_decompose",
-       "nd_rounds", "nd_round_times", "nd_rcliques", "nd_nuclei", "nd_batch_run", "nd_server_create", "nd_submit", "nd_poll", "nd_server_drain",
+       "nd_rounds", "nd_round_times", "nd_rcliques", "nd_nuclei", "nd_hierarchy", "nd_batch_run", "nd_server_create", "nd_submit", "nd_poll", "nd_server_drain",
        "nd_server_destroy", "nd_kcore_noalloc"]
 ND_NOALLOC_MAX_VERTICES = 262144
 
@@ -139,6 +139,7 @@ def lib() -> ctypes.CDLL:
         L.nd_round_times.argtypes = [vp, vp, i64]
         L.nd_rcliques.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, i64p]
         L.nd_nuclei.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, i32, vp, ctypes.c_int, i64p]
+        L.nd_hierarchy.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, ctypes.c_int, i64p]
         L.nd_kcore_noalloc.argtypes = [i32, vp, vp, vp, vp]
         L.nd_batch_run.argtypes = [vp, ctypes.POINTER(nd_request), i32, ctypes.POINTER(nd_batch_stats)]
         L.nd_server_create.argtypes = [vp, ctypes.POINTER(nd_server_cfg), ctypes.POINTER(vp)]
@@ -389,6 +390,23 @@ def nd_nuclei(g: Handle, r: int, s: int, core, level: int, out=None):
     nc = ctypes.c_int64()
     _check(lib().nd_nuclei(g.ptr, r, s, pc, int(level), po, ND_PTR_DEVICE if dev else 0, ctypes.byref(nc)))
     return out, nc.value
+
+
+def nd_hierarchy(g: Handle, r: int, s: int, core):
+    """The nucleus hierarchy (nd.h: nd_hierarchy): (comp, parent_level, parent_comp, n_nodes), int32
+    arrays of n_r following core's kind (numpy or CUDA tensor). R's node is (core[R], comp[R]); its
+    parent node is (parent_level[R], parent_comp[R]), (-1, -1) for a root."""
+    n = int(core.shape[0])
+    if _is_torch_cuda(core):
+        import torch
+        outs = [torch.empty(n, dtype=torch.int32, device=core.device) for _ in range(3)]
+    else:
+        outs = [np.empty(n, np.int32) for _ in range(3)]
+    pc, dev = _ptr(core)
+    ptrs = [_ptr(o)[0] for o in outs]
+    nn = ctypes.c_int64()
+    _check(lib().nd_hierarchy(g.ptr, r, s, pc, *ptrs, ND_PTR_DEVICE if dev else 0, ctypes.byref(nn)))
+    return outs[0], outs[1], outs[2], nn.value
 
 
 def nd_kcore_noalloc(rowptr, col, core_out, stream=None):

@@ -101,3 +101,54 @@ def test_bad_arguments(nd, ctx):
             nd.nd_nuclei(G, 1, 2, core, 0, out=torch.zeros(g.n, dtype=torch.int32, device="cuda"))
     finally:
         nd.nd_graph_free(G)
+
+
+def check_hierarchy(nd, ctx, g, r, s, device=False):
+    core = orc.decompose(g, r, s).core.astype(np.int32)
+    want = orc.hierarchy(g, r, s, core)
+    G = nd.nd_load_csr(ctx, g.rowptr, g.col, flags=nd.ND_VALIDATE)
+    try:
+        if device:
+            import torch
+
+            got = nd.nd_hierarchy(G, r, s, torch.from_numpy(core).cuda())
+            got = [x.cpu().numpy() for x in got[:3]] + [got[3]]
+        else:
+            got = nd.nd_hierarchy(G, r, s, core)
+        for name, a, b in zip(("comp", "parent_level", "parent_comp"), got[:3], want):
+            np.testing.assert_array_equal(a, b, err_msg=f"(r,s)=({r},{s}) {name}")
+        nodes = {(int(c), int(x)) for c, x in zip(core, want[0])}
+        assert got[3] == len(nodes)
+    finally:
+        nd.nd_graph_free(G)
+
+
+@pytest.mark.parametrize("r,s", RS)
+def test_hierarchy_small_graphs(nd, ctx, r, s):
+    check_hierarchy(nd, ctx, gg.fig1(), r, s)
+    check_hierarchy(nd, ctx, gg.disjoint_union(gg.complete(7), gg.fig1(), gg.complete(s), gg.complete(s + 2)), r, s)
+    for seed in range(4):
+        check_hierarchy(nd, ctx, gg.gnp(10 + 4 * seed, [0.3, 0.5, 0.7][seed % 3], 9400 + seed), r, s, device=seed % 2 == 1)
+
+
+@pytest.mark.parametrize("r,s", [(1, 2), (2, 3), (2, 4), (3, 4)])
+def test_hierarchy_power_law_and_hubs(nd, ctx, r, s):
+    check_hierarchy(nd, ctx, gg.with_planted(gg.chung_lu(1200, 5.0, 2.3, seed=9501), 10, 8, 20, 0.7, seed=9502), r, s)
+    check_hierarchy(nd, ctx, gg.hubs_over_sparse(n_common=1500, hubs=3, p_hub=0.9, avg_deg=4.0, seed=9503), r, s,
+                    device=True)
+    if s - r == 1:
+        check_hierarchy(nd, ctx, gg.rmat(11, 8, seed=9504), r, s)
+
+
+def test_hierarchy_empty_and_bad_core(nd, ctx):
+    g = gg.gnp(30, 0.0, 1)
+    check_hierarchy(nd, ctx, g, 2, 3)  # no edges: nothing to build
+    check_hierarchy(nd, ctx, g, 1, 2)  # isolated vertices: one root node each
+    G = nd.nd_load_csr(ctx, g.rowptr, g.col)
+    try:
+        with pytest.raises(nd.NdError):
+            nd.nd_hierarchy(G, 1, 2, np.full(g.n, -1, np.int32))
+        with pytest.raises(nd.NdError):
+            nd.nd_hierarchy(G, 4, 7, np.zeros(g.n, np.int32))
+    finally:
+        nd.nd_graph_free(G)
