@@ -97,3 +97,43 @@ def test_planted_communities():
     pairs = sum(s * (s - 1) // 2 for s in members)
     e = np.unique(np.minimum(u, v).astype(np.int64) * n + np.maximum(u, v)).size
     assert abs(e / pairs - p) < 0.02
+
+
+def test_batch_workload_recipe():
+    items = gg.batch_workload(64, seed=4)
+    assert len(items) == 64
+    rs_seen = set()
+    for g, rs in items:
+        assert 50 <= g.n <= 5000 and rs in [(1, 2), (2, 3), (3, 4)]
+        rs_seen.add(rs)
+    assert rs_seen == {(1, 2), (2, 3), (3, 4)}
+    for g, _ in items[:8]:
+        assert_valid_csr(g)
+    # a prefix does not depend on the count
+    again = gg.batch_workload(16, seed=4)
+    for (a, ra), (b, rb) in zip(items[:16], again):
+        assert ra == rb and np.array_equal(a.col, b.col)
+
+
+def test_serve_pool_recipe():
+    pool = gg.serve_pool(48, seed=5, max_m=60_000)
+    assert 0 < len(pool) < 48  # the draws above max_m are skipped
+    ms = np.array([g.m for g in pool])
+    assert ms.min() >= 50 and ms.max() <= 60_000 * 1.05
+    for g in pool[:6]:
+        assert_valid_csr(g)
+    # max_m skips draws without changing the others
+    full = [g for g in gg.serve_pool(48, seed=5, max_m=10**9) if g.m <= 60_000 * 1.05]
+    assert len(full) >= len(pool)
+
+
+def test_hubs_over_sparse_makes_long_lists():
+    g = gg.hubs_over_sparse(n_common=3000, hubs=3, p_hub=0.9, avg_deg=4.0, seed=7)
+    assert_valid_csr(g)
+    deg = np.diff(g.rowptr)
+    hub_deg = deg[-3:]
+    assert np.all(hub_deg > 0.85 * 3000) and np.median(deg[:-3]) < 20
+    # the hubs are mutually adjacent
+    for h in range(3000, 3003):
+        row = g.col[g.rowptr[h]:g.rowptr[h + 1]]
+        assert set(range(3000, 3003)) - {h} <= set(row.tolist())
